@@ -1,0 +1,331 @@
+/*
+ * mrip.h -- C ABI of the GB300 engine for Multiple Replications In Parallel
+ * (MRIP) of stochastic simulations.
+ *
+ * Method (Passerat-Palmbach, Caux, Siregar, Mazel, Hill, "Warp-Level
+ * Parallelism: Enabling Multiple Replications In Parallel on GPU", ESM 2011):
+ *   - Section 1: a stochastic model is run many times with independent random
+ *     sources; the replication mean, by the Central Limit Theorem, gives a
+ *     confidence interval; an experimental plan runs a set of replications
+ *     for each combination of factor levels (a "design point").
+ *   - Section 3: each replication is mapped to its own warp (WLP) rather than
+ *     to one thread (TLP).  Here the mapping is chosen per model (thread,
+ *     cooperative warp, CTA) and WLP is kept as a measurable baseline.
+ *   - Section 5.1: the models (M/M/1 queue, random walk).  This engine adds
+ *     a 3-station tandem queue, a forest-fire cellular automaton and an
+ *     L1-exit walk as workloads of the same method.
+ *
+ * Random streams.  Every replication draws from Philox4x32-10 (Salmon et al.,
+ * SC'11) with key = (seed low 32 bits, seed high 32 bits) and counter
+ *   c0 = sub-block index within a step, c1 = step index,
+ *   c2 = replication index,             c3 = (tag << 24) | design point,
+ * tags 0 simulation, 1 lattice initial state, 2 control-mean runs,
+ * 3 network initialisation, 4 minibatch order.  (The paper split one
+ * Tausworthe stream by random spacing, Section 5; a counter-based generator
+ * lets any replication be recomputed alone.)  Hence design points < 2^24 and
+ * replication indices < 2^32.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MRIP_OK or an error code; mrip_last_error() returns a
+ *     thread-local, library-owned message for the last failure on the
+ *     calling thread.  No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the current
+ *     device, owned by the caller (for instance allocated by PyTorch); "host"
+ *     pointers are ordinary host memory owned by the caller.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream only enqueue work on it and return without waiting,
+ *     unless the description says "synchronous".
+ *   - Per-replication outputs are laid out design-point-major:
+ *     element (dp, rep) sits at index dp * n_reps + rep.  Multi-valued
+ *     outputs are structure-of-arrays planes: value k of item i sits at
+ *     k * n_items + i.
+ *   - Scratch memory (work-stealing tickets, partial sums, device error
+ *     flags) is allocated by the library once per device and grown on
+ *     demand; it is freed at process exit.
+ *   - Invalid arguments return MRIP_EINVAL before anything is enqueued.
+ *   - A CUDA error returns MRIP_ECUDA with the runtime's message.
+ */
+#ifndef MRIP_H
+#define MRIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRIP_OK = 0,
+    MRIP_EINVAL = 1,        /* invalid argument                                  */
+    MRIP_ENOMEM = 2,        /* device or host allocation failed                  */
+    MRIP_ECUDA = 3,         /* CUDA runtime or launch error                      */
+    MRIP_ESTEPCAP = 4,      /* a replication hit its step cap (output set to -1) */
+    MRIP_ESTATE = 5,        /* call out of order (e.g. stats before run)         */
+    MRIP_EUNSUPPORTED = 6   /* valid request this build does not implement       */
+} mrip_status;
+
+typedef enum {
+    MRIP_MM1 = 1,
+    MRIP_TANDEM3 = 2,
+    MRIP_FOREST_FIRE = 3,
+    MRIP_WALK_L1_EXIT = 4
+} mrip_kind;
+
+/* Replication-to-hardware mappings (paper, Section 3, and its TLP baseline). */
+typedef enum {
+    MRIP_MAP_AUTO = 0,        /* use the model's plan (autotuned or default)      */
+    MRIP_MAP_THREAD = 1,      /* one replication per thread (TLP)                 */
+    MRIP_MAP_WARP_1LANE = 2,  /* one replication per warp, lane 0 only (WLP)      */
+    MRIP_MAP_WARP_COOP = 3,   /* one replication per warp, all lanes cooperate    */
+    MRIP_MAP_CTA = 4,         /* one replication per CTA (lattice models)         */
+    MRIP_MAP_PERSISTENT = 5   /* persistent work-stealing warps, lanes refilled   */
+} mrip_mapping;
+
+/* Per-design-point interval (paper, Section 1). */
+typedef struct {
+    int64_t n;          /* replications used                                    */
+    double mean;        /* replication mean                                     */
+    double var;         /* unbiased sample variance (NaN if n < 2)              */
+    double half_width;  /* t_{(1+conf)/2, df} * sqrt(var / n)  (NaN if n < 2)   */
+    double t_crit;      /* the Student-t critical value used                    */
+} mrip_stat;
+
+/* Control-variate result of one design point (df = n - 2). */
+typedef struct {
+    int64_t n;          /* held-out replications                                */
+    int64_t m;          /* control-mean runs                                    */
+    double beta;        /* Cov(Y, g) / Var(g) over the held-out replications    */
+    double mean;        /* mean(Y) - beta (mean(g) - mean(g_ctrl))              */
+    double var;         /* s_r^2 / n + beta^2 Var(g_ctrl) / m                    */
+    double half_width;  /* t_{(1+conf)/2, n-2} sqrt(var)                         */
+    double t_crit;
+} mrip_cv_stat;
+
+/* ------------------------------------------------------------------------ */
+/* Model handles (the high-level API)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Fixed parameters per model kind, passed to mrip_create_model. */
+typedef struct { int64_t n_clients; } mrip_mm1_params;
+typedef struct { int64_t n_clients; int64_t window; } mrip_tandem3_params;
+typedef struct {
+    int32_t L;          /* lattice side, multiple of 32, 32..512                 */
+    int32_t n_steps;    /* synchronous steps T >= 1                              */
+    double density;     /* initial tree probability in [0, 1)                    */
+    int32_t window;     /* early-window length for the network features (<= T)  */
+} mrip_forest_fire_params;
+typedef struct { int64_t max_steps; } mrip_walk_params;  /* <= 2^38 */
+
+typedef struct mrip_model mrip_model;   /* opaque, library-owned */
+
+/* Create a model of `kind` from its fixed-parameter struct (one of the above;
+ * params_bytes must equal its size).  The handle owns the device buffers of
+ * its runs.  Not thread-safe per handle; separate handles are independent.
+ * Errors: MRIP_EINVAL (unknown kind, wrong size, parameter out of range). */
+mrip_status mrip_create_model(int kind, const void *params, size_t params_bytes,
+                              mrip_model **out);
+
+/* Run all later work of this handle on `cuda_stream` (a cudaStream_t). */
+mrip_status mrip_set_stream(mrip_model *model, void *cuda_stream);
+
+/* Run n_reps replications of every design point (paper, Section 1: MRIP over
+ * an experimental plan) and reduce them to per-design-point (n, mean, M2) on
+ * the device.  design_points: host array, n_dp x dp_dim, row-major, with
+ * dp_dim and meaning per kind: MM1 (lambda, mu); TANDEM3 (lambda, mu1, mu2,
+ * mu3); FOREST_FIRE (p_grow, p_lightning) each in [0, 1); WALK_L1_EXIT (R),
+ * an integer 1..65536.  Rates must be finite and > 0.  The design points are
+ * copied to the device on the handle's stream; the call returns once the
+ * work is enqueued (the replay of a CUDA graph captured on first use for this
+ * shape).  Per-replication outputs stay on the device (mrip_outputs).
+ * The scalar per replication is: MM1 mean wait; TANDEM3 mean sojourn;
+ * FOREST_FIRE mean burning fraction sum_t burning_t / (T L^2); WALK tau. */
+mrip_status mrip_run(mrip_model *model, const double *design_points, int32_t n_dp,
+                     int64_t n_reps, uint64_t seed);
+
+/* Same as mrip_run with design_points already on the device. */
+mrip_status mrip_run_device(mrip_model *model, const double *d_design_points, int32_t n_dp,
+                            int64_t n_reps, uint64_t seed);
+
+/* Synchronous.  Per-design-point intervals of the last run at confidence
+ * `conf` in (0, 1) into the caller's host array out[n_dp].  Returns
+ * MRIP_ESTEPCAP if a replication hit its step cap, MRIP_ESTATE before any
+ * run. */
+mrip_status mrip_stats(mrip_model *model, double conf, mrip_stat *out);
+
+/* Synchronous.  Copy output plane `which` of the last run into dst
+ * (dst_bytes must be at least its size; on_device != 0: dst is a device
+ * pointer).  Planes: MM1 0 wait, 1 idle, 2 system (double); TANDEM3 0 Y
+ * (double), 1 features (double, 8 planes); FOREST_FIRE 0 burning counts
+ * (int32, rep-major, T per replication), 1 per-replication scalar (double);
+ * WALK 0 tau (int64).  Sizes: mrip_output_bytes. */
+mrip_status mrip_outputs(mrip_model *model, int which, void *dst, size_t dst_bytes,
+                         int on_device);
+mrip_status mrip_output_bytes(const mrip_model *model, int which, size_t *bytes);
+
+/* Choose the mapping and launch shape of this handle's model: plan_json is a
+ * small JSON object, e.g. {"mapping": 5, "warps_per_cta": 8, "ctas_per_sm": 2,
+ * "chunk": 64}; unknown keys are rejected.  mrip_get_plan writes the current
+ * plan (NUL-terminated) into buf. */
+mrip_status mrip_set_plan(mrip_model *model, const char *plan_json);
+mrip_status mrip_get_plan(const mrip_model *model, char *buf, size_t buf_bytes);
+
+/* Synchronous.  Time every candidate plan for (design_points, n_dp, n_reps)
+ * with CUDA events (best of `trials`), check that every candidate gives the
+ * same per-replication outputs as the first, keep the fastest and record it
+ * in the cache file `cache_path` (JSON lines, may be NULL).  The WLP mapping
+ * of the paper (Section 3) is one of the candidates. */
+mrip_status mrip_autotune(mrip_model *model, const double *design_points, int32_t n_dp,
+                          int64_t n_reps, uint64_t seed, int trials, const char *cache_path);
+
+/* Learned control variate (engine extension; the paper's estimator is the
+ * plain mean of Section 1).  Runs the replications, trains the network
+ * d_in -> 64 -> 64 -> 1 (d_in 8 for TANDEM3, 6 for FOREST_FIRE) on the first
+ * ceil(train_frac * n_reps) replications of every design point with the
+ * engine's own kernels, predicts the held-out replications and `m_ctrl`
+ * control-mean runs per design point (tag 2, early window only), and writes
+ * per-design-point plain (all n_reps) and control-variate intervals into the
+ * caller's host arrays.  Synchronous. */
+typedef struct {
+    double train_frac;   /* in (0, 1), e.g. 0.1                      */
+    int32_t epochs;      /* >= 1                                      */
+    int32_t batch;       /* >= 1                                      */
+    float lr, beta1, beta2, eps;
+    int64_t m_ctrl;      /* control-mean runs per design point >= 2    */
+    double conf;         /* interval confidence in (0, 1)             */
+    uint64_t net_seed;   /* network initialisation and minibatch order */
+} mrip_cv_params;
+mrip_status mrip_run_cv(mrip_model *model, const double *design_points, int32_t n_dp,
+                        int64_t n_reps, uint64_t seed, const mrip_cv_params *params,
+                        mrip_stat *plain_out, mrip_cv_stat *cv_out, float *train_loss_out);
+
+void mrip_destroy(mrip_model *model);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char *mrip_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Stage entry points (the low-level API): one per step of the hot path,     */
+/* device buffers owned by the caller.                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 of n counters.  d_ctr: device uint32 n x 4; d_key: device
+ * uint32 n x 2; d_out: device uint32 n x 4. */
+mrip_status mrip_philox(const uint32_t *d_ctr, const uint32_t *d_key, int64_t n,
+                        uint32_t *d_out, void *stream);
+
+/* u = top 53 bits of hi:lo times 2^-53 and the exponential variate
+ * -log(1 - u) / rate (paper, Section 5.1: the M/M/1 arrival gaps and service
+ * times are exponential).  All arrays device, length n. */
+mrip_status mrip_expo(const uint32_t *d_lo, const uint32_t *d_hi, const double *d_rate,
+                      int64_t n, double *d_u, double *d_e, void *stream);
+
+/* M/M/1 replications (paper, Section 5.1, second model).  d_dps: device
+ * n_dp x 2 (lambda, mu).  Client n uses block (c0 = 0, c1 = n): words 0,1 ->
+ * service S_n ~ Exp(mu), words 2,3 -> gap A_{n+1} ~ Exp(lambda); W_0 = 0,
+ * W_{n+1} = max(0, W_n + S_n - A_{n+1}).  Outputs (device, n_dp * n_reps,
+ * any may be NULL): mean wait W, mean idle max(0, A_{n+1} - W_n - S_n),
+ * mean time in system W + S over n < n_clients.  mapping: THREAD,
+ * WARP_1LANE or WARP_COOP (AUTO = THREAD). */
+mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+                              int64_t n_clients, uint64_t seed, int mapping,
+                              double *d_wait, double *d_idle, double *d_system, void *stream);
+
+/* Tandem of three M/M/1 stations.  d_dps: device n_dp x 4 (lambda, mu1..3).
+ * Client n: block (0, n) words 0,1 -> gap A_n, 2,3 -> S_{n,1}; block (1, n)
+ * -> S_{n,2}, S_{n,3}.  V_{n,j} = max(V_{n-1,j} - A_n, V_{n,j-1}) + S_{n,j},
+ * V_{n,0} = 0, V_{-1,j} = -inf; Y = mean_n V_{n,3}.  Replications
+ * rep0 .. rep0 + n_reps - 1 of stream `tag`.  d_y: device n_dp * n_reps;
+ * d_feat (may be NULL): device 8 planes of n_dp * n_reps: lambda, mu1..3 and
+ * the means over the first min(window, n_clients) clients of A, S1, S2, S3.
+ * If n_clients == window only the early window is simulated (control runs). */
+mrip_status mrip_tandem3_simulate(const double *d_dps, int32_t n_dp, int64_t rep0,
+                                  int64_t n_reps, int64_t n_clients, int64_t window,
+                                  uint64_t seed, uint32_t tag, int mapping, double *d_y,
+                                  double *d_feat, void *stream);
+
+/* Forest-fire automaton, one CTA per replication, lattice bit-packed in
+ * registers and shared memory.  d_dps: device n_dp x 2 (p_grow,
+ * p_lightning).  L multiple of 32 in 32..512, n_steps >= 0.
+ * Initial state from tag 1 (tree iff word < floor(density 2^32)), or from
+ * d_init (device uint8 L*L per replication, states 0/1/2; may be NULL).
+ * Step t uses word (i mod 4) of block (i div 4, t) for cell i = y L + x:
+ * burning -> empty; tree -> burning if a von Neumann neighbour burns or the
+ * word < floor(p_lightning 2^32); empty -> tree iff word < floor(p_grow
+ * 2^32).  Outputs (device, may be NULL): d_counts int32 [n_dp*n_reps][n_steps]
+ * burning cells after each step; d_scalar double [n_dp*n_reps] =
+ * sum_t counts / (n_steps L^2); d_final uint8 [n_dp*n_reps][L*L]. */
+mrip_status mrip_forest_fire_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+                                      int32_t L, int32_t n_steps, double density,
+                                      uint64_t seed, const uint8_t *d_init,
+                                      int32_t *d_counts, double *d_scalar, uint8_t *d_final,
+                                      void *stream);
+
+/* L1-exit walk: simple random walk on Z^2 from the origin; move m reads the
+ * 2-bit field k = m mod 64 of block (0, m div 64): word k div 16, bits
+ * 2(k mod 16)..+1; 0:+x 1:-x 2:+y 3:-y.  tau = moves made when |x|+|y|
+ * first reaches R.  radii: HOST array n_dp (integers 1..65536).  d_tau:
+ * device int64 n_dp * n_reps (-1 where max_steps was reached, and the call's
+ * later status check reports MRIP_ESTEPCAP).  mapping: THREAD, WARP_1LANE,
+ * WARP_COOP or PERSISTENT (AUTO = PERSISTENT); warps_per_cta, ctas_per_sm and
+ * chunk (replications per ticket) shape PERSISTENT (0 = default). */
+mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t n_reps,
+                               uint64_t seed, int64_t max_steps, int mapping,
+                               int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk,
+                               int64_t *d_tau, void *stream);
+
+/* Synchronous.  MRIP_ESTEPCAP if any walk launched since the last check hit
+ * its step cap (and clears the flag), else MRIP_OK. */
+mrip_status mrip_check_device_flags(void);
+
+/* Per-design-point (n, mean, M2) of d_x (device double [n_dp][n_reps]) by
+ * Welford within a thread and a Chan merge across threads in a fixed tree
+ * (deterministic).  d_out: device double [n_dp][3]. */
+mrip_status mrip_stats_reduce(const double *d_x, int32_t n_dp, int64_t n_reps,
+                              double *d_out, void *stream);
+
+/* Host, synchronous: intervals from host (n, mean, M2) triples. */
+mrip_status mrip_stats_finalize(const double *nmm2, int32_t n_dp, double conf,
+                                mrip_stat *out);
+
+/* Host: Student-t critical value t with P(T > t) = (1 - conf) / 2, df >= 1. */
+mrip_status mrip_t_crit(double conf, int64_t df, double *out);
+
+/* ----- learned control variate: network stages (device, caller-owned) ---- */
+/* Flat FP32 parameter vector of d_in -> 64 -> 64 -> 1:
+ * W1 [64][d_in], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1]. */
+int64_t mrip_mlp_param_count(int32_t d_in);
+
+/* He-uniform initialisation from stream tag 3 (weights), zero biases. */
+mrip_status mrip_mlp_init(int32_t d_in, uint64_t seed, float *d_theta, void *stream);
+
+/* Forward pass of n samples.  d_x: device float [d_in][n] planes
+ * (standardised inputs); d_yhat: device float n.  BF16 operands, FP32
+ * accumulation. */
+mrip_status mrip_mlp_forward(const float *d_theta, int32_t d_in, const float *d_x,
+                             int64_t n, float *d_yhat, void *stream);
+
+/* Loss mean (yhat - y)^2 over the B samples idx[0..B) (device int64, may be
+ * NULL = 0..B-1) and its gradient.  d_grad: device float param_count;
+ * d_loss: device float 1 (may be NULL). */
+mrip_status mrip_mlp_loss_grad(const float *d_theta, int32_t d_in, const float *d_x,
+                               const float *d_y, int64_t n, const int64_t *d_idx,
+                               int64_t B, float *d_grad, float *d_loss, void *stream);
+
+/* One Adam step (Kingma & Ba) with bias correction; step t >= 1. */
+mrip_status mrip_adam_step(float *d_theta, float *d_m, float *d_v, const float *d_grad,
+                           int64_t n, int64_t t, float lr, float beta1, float beta2,
+                           float eps, void *stream);
+
+/* Control-variate estimator of n_dp design points (FP64, device): d_y, d_g
+ * [n_dp][n]; d_gc [n_dp][m].  d_out: device double [n_dp][5] =
+ * (beta, mean, var, y_mean, 0); the host adds the t critical value. */
+mrip_status mrip_cv_reduce(const double *d_y, const double *d_g, int64_t n,
+                           const double *d_gc, int64_t m, int32_t n_dp, double *d_out,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRIP_H */

@@ -1,0 +1,302 @@
+// Queueing models of the MRIP engine: the M/M/1 queue of the paper
+// (Section 5.1, second model) and a 3-station tandem of M/M/1 stations.
+//
+// Mappings (paper, Section 3):
+//   THREAD      one replication per thread (TLP);
+//   WARP_1LANE  one replication per warp, lane 0 works, 31 lanes idle (WLP);
+//   WARP_COOP   one replication per warp, the clients split into 32
+//               contiguous segments.  The Lindley step W -> max(0, W + S - A)
+//               composes to maps W -> max(c, W + d); lanes compose their
+//               segment's map, a warp scan of the maps gives each segment's
+//               entry wait, and each lane then replays its segment with the
+//               plain recurrence.
+#include "common.cuh"
+
+namespace mrip {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct Mm1Out {
+    double* wait;
+    double* idle;
+    double* system;
+};
+
+// Client n of (dp, rep): service S_n from words (0,1), gap A_{n+1} from (2,3).
+__device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp, double lam,
+                                           double mu, const RoundKeys& rk, double& s, double& a) {
+    const uint4 b = philox(0u, n, rep, stream_word(0u, dp), rk);
+    s = expo_div(u53(b.x, b.y), mu);
+    a = expo_div(u53(b.z, b.w), lam);
+}
+
+template <bool kLane0Only>
+__global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
+                                  long long n_reps, long long n_clients,
+                                  const __grid_constant__ RoundKeys rk, Mm1Out out) {
+    long long item;
+    if (kLane0Only) {
+        if ((threadIdx.x & 31) != 0) return;
+        item = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    } else {
+        item = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    }
+    if (item >= n_items) return;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    double w = 0.0, sum_w = 0.0, sum_i = 0.0, sum_v = 0.0;
+    for (long long n = 0; n < n_clients; ++n) {
+        double s, a;
+        mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+        sum_w += w;
+        const double v = w + s;
+        sum_v += v;
+        const double t = v - a;
+        sum_i += (t < 0.0) ? -t : 0.0;
+        w = (t > 0.0) ? t : 0.0;
+    }
+    const double inv = static_cast<double>(n_clients);
+    if (out.wait) out.wait[item] = sum_w / inv;
+    if (out.idle) out.idle[item] = sum_i / inv;
+    if (out.system) out.system[item] = sum_v / inv;
+}
+
+// Max-plus map W -> max(c, W + d).  compose(first, then).
+struct MaxPlus {
+    double c, d;
+};
+__device__ __forceinline__ MaxPlus compose(MaxPlus f, MaxPlus g) {
+    // g(f(W)) = max(g.c, max(f.c, W + f.d) + g.d) = max(max(g.c, f.c + g.d), W + (f.d + g.d))
+    MaxPlus r;
+    const double cc = f.c + g.d;
+    r.c = (g.c > cc) ? g.c : cc;
+    r.d = f.d + g.d;
+    return r;
+}
+
+// One warp per replication; clients staged in shared memory when kStage.
+template <bool kStage>
+__global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n_items,
+                                     long long n_reps, long long n_clients,
+                                     const __grid_constant__ RoundKeys rk, Mm1Out out) {
+    extern __shared__ double stage[];  // per warp: S[seg_cap*32], A[seg_cap*32]
+    const int lane = threadIdx.x & 31;
+    const int warp_in_cta = threadIdx.x >> 5;
+    const long long item = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    if (item >= n_items) return;  // warp-uniform
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    const long long seg = (n_clients + 31) / 32;
+    const long long lo = lane * seg;
+    const long long hi = (lo + seg < n_clients) ? lo + seg : n_clients;
+    double* s_buf = stage + static_cast<size_t>(warp_in_cta) * 2 * seg * 32;
+    double* a_buf = s_buf + seg * 32;
+
+    // pass 1: the segment's composed map
+    MaxPlus f{-INFINITY, 0.0};
+    for (long long n = lo; n < hi; ++n) {
+        double s, a;
+        mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+        if (kStage) {
+            s_buf[(n - lo) * 32 + lane] = s;
+            a_buf[(n - lo) * 32 + lane] = a;
+        }
+        MaxPlus step{0.0, s - a};
+        f = compose(f, step);
+    }
+    // inclusive scan of maps over lanes (earlier lanes first), then shift
+    MaxPlus acc = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        MaxPlus prev;
+        prev.c = __shfl_up_sync(kFull, acc.c, off);
+        prev.d = __shfl_up_sync(kFull, acc.d, off);
+        if (lane >= off) acc = compose(prev, acc);
+    }
+    MaxPlus excl;
+    excl.c = __shfl_up_sync(kFull, acc.c, 1);
+    excl.d = __shfl_up_sync(kFull, acc.d, 1);
+    double w = 0.0;
+    if (lane > 0) w = (excl.c > excl.d) ? excl.c : excl.d;  // entry wait = map(0)
+
+    // pass 2: replay the segment with the plain recurrence
+    double sum_w = 0.0, sum_i = 0.0, sum_v = 0.0;
+    for (long long n = lo; n < hi; ++n) {
+        double s, a;
+        if (kStage) {
+            s = s_buf[(n - lo) * 32 + lane];
+            a = a_buf[(n - lo) * 32 + lane];
+        } else {
+            mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+        }
+        sum_w += w;
+        const double v = w + s;
+        sum_v += v;
+        const double t = v - a;
+        sum_i += (t < 0.0) ? -t : 0.0;
+        w = (t > 0.0) ? t : 0.0;
+    }
+    // fixed-order (lane-ordered tree) reduction of the three sums
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double ow = __shfl_down_sync(kFull, sum_w, off);
+        const double oi = __shfl_down_sync(kFull, sum_i, off);
+        const double ov = __shfl_down_sync(kFull, sum_v, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            sum_w += ow;
+            sum_i += oi;
+            sum_v += ov;
+        }
+    }
+    if (lane == 0) {
+        const double inv = static_cast<double>(n_clients);
+        if (out.wait) out.wait[item] = sum_w / inv;
+        if (out.idle) out.idle[item] = sum_i / inv;
+        if (out.system) out.system[item] = sum_v / inv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tandem: V_{n,j} = max(V_{n-1,j} - A_n, V_{n,j-1}) + S_{n,j}
+// ---------------------------------------------------------------------------
+struct TandemOut {
+    double* y;
+    double* feat;     // 8 planes of n_items (may be null)
+    long long plane;  // plane stride = n_items
+};
+
+template <bool kLane0Only>
+__global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long n_items,
+                                      long long n_reps, long long rep0, long long n_clients,
+                                      long long window, uint32_t tag,
+                                      const __grid_constant__ RoundKeys rk, TandemOut out) {
+    long long item;
+    if (kLane0Only) {
+        if ((threadIdx.x & 31) != 0) return;
+        item = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    } else {
+        item = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    }
+    if (item >= n_items) return;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
+    const double lam = dps[4 * dp], mu1 = dps[4 * dp + 1], mu2 = dps[4 * dp + 2],
+                 mu3 = dps[4 * dp + 3];
+    const uint32_t c3 = stream_word(tag, dp);
+    const long long w_len = (n_clients < window) ? n_clients : window;
+    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
+    double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
+    for (long long n = 0; n < n_clients; ++n) {
+        const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+        const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+        const double a = expo_div(u53(b0.x, b0.y), lam);
+        const double s1 = expo_div(u53(b0.z, b0.w), mu1);
+        const double s2 = expo_div(u53(b1.x, b1.y), mu2);
+        const double s3 = expo_div(u53(b1.z, b1.w), mu3);
+        double q = v1 - a;
+        v1 = ((q > 0.0) ? q : 0.0) + s1;
+        q = v2 - a;
+        v2 = ((q > v1) ? q : v1) + s2;
+        q = v3 - a;
+        v3 = ((q > v2) ? q : v2) + s3;
+        sum_y += v3;
+        if (n < w_len) {
+            sum_a += a;
+            sum_1 += s1;
+            sum_2 += s2;
+            sum_3 += s3;
+        }
+    }
+    out.y[item] = sum_y / static_cast<double>(n_clients);
+    if (out.feat) {
+        const double wl = static_cast<double>(w_len);
+        double* f = out.feat + item;
+        const long long p = out.plane;
+        f[0] = lam;
+        f[p] = mu1;
+        f[2 * p] = mu2;
+        f[3 * p] = mu3;
+        f[4 * p] = sum_a / wl;
+        f[5 * p] = sum_1 / wl;
+        f[6 * p] = sum_2 / wl;
+        f[7 * p] = sum_3 / wl;
+    }
+}
+
+}  // namespace
+}  // namespace mrip
+
+using namespace mrip;
+
+extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+                                         int64_t n_clients, uint64_t seed, int mapping,
+                                         double* d_wait, double* d_idle, double* d_system,
+                                         void* stream) {
+    if (n_dp < 0 || n_reps < 0 || n_clients < 1)
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: need n_dp >= 0, n_reps >= 0, n_clients >= 1");
+    if (n_dp >= (1 << 24) || n_reps > 0xFFFFFFFFll || n_clients > 0xFFFFFFFFll)
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: n_dp < 2^24, n_reps and n_clients <= 2^32-1");
+    const long long n_items = static_cast<long long>(n_dp) * n_reps;
+    if (n_items == 0) return MRIP_OK;
+    if (!d_dps) return fail(MRIP_EINVAL, "mrip_mm1_simulate: null design points");
+    const RoundKeys rk = expand_key(seed);
+    Mm1Out out{d_wait, d_idle, d_system};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
+        mm1_serial_kernel<false><<<ceil_div_u(n_items, 128), 128, 0, st>>>(
+            d_dps, n_items, n_reps, n_clients, rk, out);
+    } else if (mapping == MRIP_MAP_WARP_1LANE) {
+        mm1_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
+            d_dps, n_items, n_reps, n_clients, rk, out);
+    } else if (mapping == MRIP_MAP_WARP_COOP) {
+        const long long seg = (n_clients + 31) / 32;
+        const size_t per_warp = static_cast<size_t>(seg) * 32 * 2 * sizeof(double);
+        const int warps = 1;
+        if (per_warp * warps <= 96 * 1024) {
+            const size_t smem = per_warp * warps;
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(mm1_warp_coop_kernel<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem));
+            mm1_warp_coop_kernel<true><<<ceil_div_u(n_items, warps), 32 * warps, smem, st>>>(
+                d_dps, n_items, n_reps, n_clients, rk, out);
+        } else {
+            mm1_warp_coop_kernel<false><<<ceil_div_u(n_items, 4), 128, 0, st>>>(
+                d_dps, n_items, n_reps, n_clients, rk, out);
+        }
+    } else {
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");
+    }
+    return launch_status("mrip_mm1_simulate");
+}
+
+extern "C" mrip_status mrip_tandem3_simulate(const double* d_dps, int32_t n_dp, int64_t rep0,
+                                             int64_t n_reps, int64_t n_clients, int64_t window,
+                                             uint64_t seed, uint32_t tag, int mapping,
+                                             double* d_y, double* d_feat, void* stream) {
+    if (n_dp < 0 || n_reps < 0 || rep0 < 0 || n_clients < 1 || window < 1)
+        return fail(MRIP_EINVAL,
+                    "mrip_tandem3_simulate: need n_dp, n_reps, rep0 >= 0 and n_clients, window >= 1");
+    if (n_dp >= (1 << 24) || rep0 + n_reps > 0x100000000ll || n_clients > 0xFFFFFFFFll || tag > 255)
+        return fail(MRIP_EINVAL,
+                    "mrip_tandem3_simulate: n_dp < 2^24, replication indices < 2^32, tag < 256");
+    const long long n_items = static_cast<long long>(n_dp) * n_reps;
+    if (n_items == 0) return MRIP_OK;
+    if (!d_dps || !d_y) return fail(MRIP_EINVAL, "mrip_tandem3_simulate: null pointer");
+    const RoundKeys rk = expand_key(seed);
+    TandemOut out{d_y, d_feat, n_items};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
+        tandem3_serial_kernel<false><<<ceil_div_u(n_items, 128), 128, 0, st>>>(
+            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, out);
+    } else if (mapping == MRIP_MAP_WARP_1LANE) {
+        tandem3_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
+            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, out);
+    } else {
+        return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD or WARP_1LANE");
+    }
+    return launch_status("mrip_tandem3_simulate");
+}

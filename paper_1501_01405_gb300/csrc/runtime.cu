@@ -1,0 +1,161 @@
+// Library runtime: thread-local error state, per-device scratch memory,
+// device error flags, and the random-stream stage entry points
+// (mrip_philox, mrip_expo).
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mrip {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct DeviceScratch {
+    void* ptr[8] = {nullptr};
+    size_t bytes[8] = {0};
+    int* flags = nullptr;
+    int sms = 0;
+};
+std::mutex g_scratch_mutex;
+std::vector<DeviceScratch> g_scratch;
+
+DeviceScratch& dev_scratch() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (static_cast<int>(g_scratch.size()) <= dev) g_scratch.resize(dev + 1);
+    return g_scratch[dev];
+}
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+mrip_status fail(mrip_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+mrip_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MRIP_OK;
+    return fail(MRIP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+mrip_status launch_status(const char* what) { return cuda_status(cudaGetLastError(), what); }
+
+void* scratch(size_t bytes, int slot) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    DeviceScratch& d = dev_scratch();
+    if (d.bytes[slot] >= bytes && d.ptr[slot]) return d.ptr[slot];
+    if (d.ptr[slot]) {
+        cudaDeviceSynchronize();  // the old buffer may still be in use
+        cudaFree(d.ptr[slot]);
+        d.ptr[slot] = nullptr;
+        d.bytes[slot] = 0;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    if (cudaMalloc(&d.ptr[slot], want) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    d.bytes[slot] = want;
+    return d.ptr[slot];
+}
+
+int* device_error_flags() {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    DeviceScratch& d = dev_scratch();
+    if (!d.flags) {
+        if (cudaMalloc(&d.flags, 16 * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            d.flags = nullptr;
+            return nullptr;
+        }
+        cudaMemset(d.flags, 0, 16 * sizeof(int));
+    }
+    return d.flags;
+}
+
+int sm_count() {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    DeviceScratch& d = dev_scratch();
+    if (d.sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (d.sms <= 0) d.sms = 1;
+    }
+    return d.sms;
+}
+
+// ---------------------------------------------------------------------------
+// Random-stream stages
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(const uint4* __restrict__ ctr, const uint2* __restrict__ key,
+                              long long n, uint4* __restrict__ out) {
+    long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    uint4 c = ctr[i];
+    uint2 k = key[i];
+    uint32_t a = k.x, b = k.y;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        philox_round(c.x, c.y, c.z, c.w, a, b);
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    out[i] = c;
+}
+
+__global__ void expo_kernel(const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi,
+                            const double* __restrict__ rate, long long n, double* __restrict__ u_out,
+                            double* __restrict__ e_out) {
+    long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    double u = u53(lo[i], hi[i]);
+    if (u_out) u_out[i] = u;
+    if (e_out) e_out[i] = expo_div(u, rate[i]);
+}
+
+}  // namespace mrip
+
+using namespace mrip;
+
+extern "C" const char* mrip_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" mrip_status mrip_philox(const uint32_t* d_ctr, const uint32_t* d_key, int64_t n,
+                                   uint32_t* d_out, void* stream) {
+    if (n < 0) return fail(MRIP_EINVAL, "mrip_philox: n < 0");
+    if (n == 0) return MRIP_OK;
+    if (!d_ctr || !d_key || !d_out) return fail(MRIP_EINVAL, "mrip_philox: null pointer");
+    if ((reinterpret_cast<uintptr_t>(d_ctr) | reinterpret_cast<uintptr_t>(d_out)) & 15u ||
+        reinterpret_cast<uintptr_t>(d_key) & 7u)
+        return fail(MRIP_EINVAL, "mrip_philox: misaligned buffer (ctr/out need 16 B, key 8 B)");
+    philox_kernel<<<ceil_div_u(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const uint4*>(d_ctr), reinterpret_cast<const uint2*>(d_key), n,
+        reinterpret_cast<uint4*>(d_out));
+    return launch_status("mrip_philox");
+}
+
+extern "C" mrip_status mrip_expo(const uint32_t* d_lo, const uint32_t* d_hi, const double* d_rate,
+                                 int64_t n, double* d_u, double* d_e, void* stream) {
+    if (n < 0) return fail(MRIP_EINVAL, "mrip_expo: n < 0");
+    if (n == 0) return MRIP_OK;
+    if (!d_lo || !d_hi || (d_e && !d_rate)) return fail(MRIP_EINVAL, "mrip_expo: null pointer");
+    expo_kernel<<<ceil_div_u(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_lo, d_hi, d_rate, n, d_u, d_e);
+    return launch_status("mrip_expo");
+}
+
+extern "C" mrip_status mrip_check_device_flags(void) {
+    int* flags = device_error_flags();
+    if (!flags) return fail(MRIP_ENOMEM, "device error flags: allocation failed");
+    int host[16];
+    cudaError_t e = cudaMemcpy(host, flags, sizeof(host), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e, "mrip_check_device_flags");
+    if (host[0] != 0) {
+        cudaMemset(flags, 0, sizeof(host));
+        return fail(MRIP_ESTEPCAP, "a replication reached its step cap (its output is -1)");
+    }
+    return MRIP_OK;
+}

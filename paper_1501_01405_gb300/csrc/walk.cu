@@ -1,0 +1,344 @@
+// L1-exit random walk: the uneven-length workload.  A simple random walk on
+// Z^2 starts at the origin; tau is the number of moves until |x| + |y| = R.
+// It adapts the random-walk model of the paper (Section 5.1, third model),
+// whose WLP-versus-TLP comparison is the paper's central experiment
+// (Section 5.3); stopping times vary over orders of magnitude, which is
+// what the persistent work-stealing mapping is for.
+//
+// Move m reads the 2-bit field (m mod 64) of Philox block (c0 = 0,
+// c1 = m div 64): word (m mod 64) div 16, bits 2 (m mod 16) and up.  Sixteen
+// moves of one word are applied at once (their net displacement by popcount)
+// whenever the walker is more than 16 away from the boundary; otherwise
+// move by move with an exit check.  Both paths give the same walk.
+//
+// Mappings:
+//   PERSISTENT  #SM x k CTAs; each warp takes chunks of replications from a
+//               global ticket (atomicAdd) and refills a lane as soon as its
+//               walker exits, so lanes stay busy despite uneven lengths.
+//   THREAD      one replication per thread (TLP), no refill.
+//   WARP_1LANE  one replication per warp, lane 0 only (the paper's WLP).
+//   WARP_COOP   one replication per warp: the 32 lanes take 32 consecutive
+//               16-move words, a warp scan of their displacements gives each
+//               lane's start, and a ballot finds the first exit.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mrip {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kEven = 0x55555555u;
+
+struct WalkJob {
+    const int32_t* radius;  // by processing position k
+    const int32_t* dp_of;   // design point by processing position k
+    long long n_reps;
+    long long total;
+    long long max_steps;
+    long long chunk;
+    int64_t* tau;
+    unsigned long long* ticket;
+    int* err;
+};
+
+// Net displacement of the 16 moves packed in w.
+__device__ __forceinline__ void word_displacement(uint32_t w, int& dx, int& dy) {
+    const uint32_t sgn = w & kEven;
+    const uint32_t axis = (w >> 1) & kEven;
+    const int nx = __popc(~axis & kEven);
+    dx = nx - 2 * __popc(~axis & sgn);
+    dy = (16 - nx) - 2 * __popc(axis & sgn);
+}
+
+// Apply the 16 moves of w one by one from (x, y); returns the 1-based index
+// of the exiting move, or 0 (then (x, y) is the end point).
+__device__ __forceinline__ int word_steps(uint32_t w, int R, int& x, int& y) {
+#pragma unroll 4
+    for (int s = 0; s < 16; ++s) {
+        const uint32_t f = (w >> (2 * s)) & 3u;
+        const int step = 1 - 2 * static_cast<int>(f & 1u);
+        if (f & 2u)
+            y += step;
+        else
+            x += step;
+        if (abs(x) + abs(y) >= R) return s + 1;
+    }
+    return 0;
+}
+
+// Advance through the 64 moves of one block; true on exit (m = tau).
+__device__ __forceinline__ bool walk_block(const uint4 b, int R, int& x, int& y, long long& m) {
+    const uint32_t words[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t w = words[k];
+        if (abs(x) + abs(y) + 16 < R) {
+            int dx, dy;
+            word_displacement(w, dx, dy);
+            x += dx;
+            y += dy;
+            m += 16;
+        } else {
+            const int e = word_steps(w, R, x, y);
+            if (e) {
+                m += e;
+                return true;
+            }
+            m += 16;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void decode(const WalkJob& job, long long g, int& R, uint32_t& dp,
+                                       uint32_t& rep, long long& out) {
+    const long long k = g / job.n_reps;
+    rep = static_cast<uint32_t>(g - k * job.n_reps);
+    R = job.radius[k];
+    dp = static_cast<uint32_t>(job.dp_of[k]);
+    out = static_cast<long long>(dp) * job.n_reps + rep;
+}
+
+// Whole replication on one thread (THREAD and WARP_1LANE mappings).
+__device__ void walk_serial(const WalkJob& job, long long g, const RoundKeys& rk) {
+    int R;
+    uint32_t dp, rep;
+    long long out;
+    decode(job, g, R, dp, rep, out);
+    int x = 0, y = 0;
+    long long m = 0;
+    const uint32_t c3 = stream_word(0u, dp);
+    while (true) {
+        const uint4 b = philox(0u, static_cast<uint32_t>(m >> 6), rep, c3, rk);
+        if (walk_block(b, R, x, y, m)) {
+            if (m > job.max_steps) break;
+            job.tau[out] = m;
+            return;
+        }
+        if (m >= job.max_steps) break;
+    }
+    job.tau[out] = -1;
+    atomicExch(job.err, 1);
+}
+
+template <bool kLane0Only>
+__global__ void walk_serial_kernel(WalkJob job, const __grid_constant__ RoundKeys rk) {
+    long long g;
+    if (kLane0Only) {
+        if ((threadIdx.x & 31) != 0) return;
+        g = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    } else {
+        g = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    }
+    if (g >= job.total) return;
+    walk_serial(job, g, rk);
+}
+
+__global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ RoundKeys rk) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    bool active = false;
+    int x = 0, y = 0, R = 0;
+    long long m = 0, out = 0;
+    uint32_t dp = 0, rep = 0, c3 = 0;
+    long long next = 0, end = 0;  // warp-uniform range of the current chunk
+    bool exhausted = false;       // warp-uniform
+    while (true) {
+        unsigned need = __ballot_sync(kFull, !active);
+        while (need && !exhausted) {
+            if (next >= end) {
+                unsigned long long start = 0;
+                if (lane == 0) start = atomicAdd(job.ticket, static_cast<unsigned long long>(job.chunk));
+                start = __shfl_sync(kFull, start, 0);
+                if (static_cast<long long>(start) >= job.total) {
+                    exhausted = true;
+                    break;
+                }
+                next = static_cast<long long>(start);
+                end = next + job.chunk < job.total ? next + job.chunk : job.total;
+            }
+            const long long g = next + __popc(need & below);
+            const bool take = ((need >> lane) & 1u) && g < end;
+            if (take) {
+                decode(job, g, R, dp, rep, out);
+                c3 = stream_word(0u, dp);
+                x = 0;
+                y = 0;
+                m = 0;
+                active = true;
+            }
+            const unsigned took = __ballot_sync(kFull, take);
+            next += __popc(took);
+            need &= ~took;
+        }
+        if (!__any_sync(kFull, active)) break;
+        if (active) {
+            const uint4 b = philox(0u, static_cast<uint32_t>(m >> 6), rep, c3, rk);
+            if (walk_block(b, R, x, y, m)) {
+                if (m > job.max_steps) {
+                    job.tau[out] = -1;
+                    atomicExch(job.err, 1);
+                } else {
+                    job.tau[out] = m;
+                }
+                active = false;
+            } else if (m >= job.max_steps) {
+                job.tau[out] = -1;
+                atomicExch(job.err, 1);
+                active = false;
+            }
+        }
+    }
+}
+
+// One replication per warp; lanes cover 512 consecutive moves per round.
+__global__ void walk_warp_coop_kernel(WalkJob job, const __grid_constant__ RoundKeys rk) {
+    const int lane = threadIdx.x & 31;
+    const long long g = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    if (g >= job.total) return;  // warp-uniform
+    int R;
+    uint32_t dp, rep;
+    long long out;
+    decode(job, g, R, dp, rep, out);
+    const uint32_t c3 = stream_word(0u, dp);
+    int px = 0, py = 0;  // warp-uniform position before the round
+    long long m = 0;     // warp-uniform move count before the round (multiple of 512)
+    long long result = -1;
+    while (m < job.max_steps) {
+        const uint4 b = philox(0u, static_cast<uint32_t>((m >> 6) + (lane >> 2)), rep, c3, rk);
+        const int sel = lane & 3;
+        const uint32_t w = sel == 0 ? b.x : sel == 1 ? b.y : sel == 2 ? b.z : b.w;
+        int dx, dy;
+        word_displacement(w, dx, dy);
+        int sx = dx, sy = dy;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int ox = __shfl_up_sync(kFull, sx, off);
+            const int oy = __shfl_up_sync(kFull, sy, off);
+            if (lane >= off) {
+                sx += ox;
+                sy += oy;
+            }
+        }
+        int x = px + sx - dx, y = py + sy - dy;
+        int e = 0;
+        if (abs(x) + abs(y) + 16 >= R) e = word_steps(w, R, x, y);
+        const unsigned hit = __ballot_sync(kFull, e != 0);
+        if (hit) {
+            const int first = __ffs(hit) - 1;
+            const int ef = __shfl_sync(kFull, e, first);
+            result = m + 16LL * first + ef;
+            break;
+        }
+        px += __shfl_sync(kFull, sx, 31);
+        py += __shfl_sync(kFull, sy, 31);
+        m += 512;
+    }
+    if (lane == 0) {
+        if (result < 0 || result > job.max_steps) {
+            job.tau[out] = -1;
+            atomicExch(job.err, 1);
+        } else {
+            job.tau[out] = result;
+        }
+    }
+}
+
+}  // namespace
+
+// Launch on device-resident (radius, dp) tables in processing order.
+mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_pos, int32_t n_dp,
+                        int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
+                        int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
+                        unsigned long long* d_ticket, cudaStream_t st) {
+    WalkJob job;
+    job.radius = d_radius_by_pos;
+    job.dp_of = d_dp_by_pos;
+    job.n_reps = n_reps;
+    job.total = static_cast<long long>(n_dp) * n_reps;
+    job.max_steps = max_steps;
+    job.chunk = chunk > 0 ? chunk : 64;
+    job.tau = d_tau;
+    job.ticket = d_ticket;
+    job.err = device_error_flags();
+    if (!job.err) return fail(MRIP_ENOMEM, "walk: device error flag allocation failed");
+    const RoundKeys rk = expand_key(seed);
+    if (job.total == 0) return MRIP_OK;
+    if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_PERSISTENT) {
+        const int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
+        const int cps = ctas_per_sm > 0 ? ctas_per_sm : 4;
+        if (wpc > 32 || cps > 64) return fail(MRIP_EINVAL, "walk: warps_per_cta <= 32, ctas_per_sm <= 64");
+        if (!d_ticket) return fail(MRIP_EINVAL, "walk: persistent mapping needs a ticket counter");
+        cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return cuda_status(e, "walk: ticket reset");
+        walk_persistent_kernel<<<sm_count() * cps, 32 * wpc, 0, st>>>(job, rk);
+    } else if (mapping == MRIP_MAP_THREAD) {
+        walk_serial_kernel<false><<<ceil_div_u(job.total, 128), 128, 0, st>>>(job, rk);
+    } else if (mapping == MRIP_MAP_WARP_1LANE) {
+        walk_serial_kernel<true><<<ceil_div_u(job.total * 32, 128), 128, 0, st>>>(job, rk);
+    } else if (mapping == MRIP_MAP_WARP_COOP) {
+        walk_warp_coop_kernel<<<ceil_div_u(job.total * 32, 128), 128, 0, st>>>(job, rk);
+    } else {
+        return fail(MRIP_EINVAL, "walk: unknown mapping");
+    }
+    return launch_status("walk");
+}
+
+// Host-side validation and processing order: largest radius first, so the
+// longest replications start early and the tail is short.
+mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>& r_by_pos,
+                        std::vector<int32_t>& dp_by_pos) {
+    r_by_pos.resize(n_dp);
+    dp_by_pos.resize(n_dp);
+    std::vector<int32_t> order(n_dp);
+    for (int32_t i = 0; i < n_dp; ++i) {
+        const double r = radii[i];
+        if (!(r >= 1.0 && r <= 65536.0) || r != static_cast<double>(static_cast<int32_t>(r)))
+            return fail(MRIP_EINVAL, "walk: R must be an integer in 1..65536");
+        order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return radii[a] > radii[b]; });
+    for (int32_t k = 0; k < n_dp; ++k) {
+        dp_by_pos[k] = order[k];
+        r_by_pos[k] = static_cast<int32_t>(radii[order[k]]);
+    }
+    return MRIP_OK;
+}
+
+}  // namespace mrip
+
+using namespace mrip;
+
+extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int64_t n_reps,
+                                          uint64_t seed, int64_t max_steps, int mapping,
+                                          int32_t warps_per_cta, int32_t ctas_per_sm,
+                                          int32_t chunk, int64_t* d_tau, void* stream) {
+    if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_walk_simulate: negative size");
+    if (n_dp >= (1 << 24) || n_reps > 0xFFFFFFFFll)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate: n_dp < 2^24 and n_reps < 2^32");
+    if (max_steps < 1 || max_steps > (1LL << 38))
+        return fail(MRIP_EINVAL, "mrip_walk_simulate: max_steps in 1..2^38");
+    if (chunk < 0 || chunk > (1 << 20)) return fail(MRIP_EINVAL, "mrip_walk_simulate: chunk in 0..2^20");
+    if (static_cast<long long>(n_dp) * n_reps == 0) return MRIP_OK;
+    if (!radii || !d_tau) return fail(MRIP_EINVAL, "mrip_walk_simulate: null pointer");
+    std::vector<int32_t> r_by_pos, dp_by_pos;
+    mrip_status s = walk_tables(radii, n_dp, r_by_pos, dp_by_pos);
+    if (s != MRIP_OK) return s;
+    // tables and ticket in scratch slot 0: [ticket 256 B][radius][dp]
+    const size_t tab = static_cast<size_t>(n_dp) * sizeof(int32_t);
+    char* base = static_cast<char*>(scratch(256 + 2 * tab, 0));
+    if (!base) return fail(MRIP_ENOMEM, "mrip_walk_simulate: scratch allocation failed");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t* d_r = reinterpret_cast<int32_t*>(base + 256);
+    int32_t* d_d = reinterpret_cast<int32_t*>(base + 256 + tab);
+    cudaError_t e = cudaMemcpyAsync(d_r, r_by_pos.data(), tab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_d, dp_by_pos.data(), tab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors die at return
+    if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate: table upload");
+    return walk_launch(d_r, d_d, n_dp, n_reps, seed, max_steps, mapping, warps_per_cta, ctas_per_sm,
+                       chunk, d_tau, reinterpret_cast<unsigned long long*>(base), st);
+}

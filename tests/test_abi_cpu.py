@@ -1,0 +1,123 @@
+"""The engine library loads and exports every entry point of include/mrip.h,
+and its host-only entry points behave (CPU only; no kernel is launched).
+
+* every function declared in the header is exported by libmrip.so;
+* the host Student-t critical value equals the oracle's;
+* mrip_stats_finalize (host) turns (n, mean, M2) into the oracle's interval;
+* argument validation returns MRIP_EINVAL before any CUDA work.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.stats as ostats
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mrip.h")
+
+
+def _engine():
+    eng = pytest.importorskip("paper_1501_01405_gb300")
+    try:
+        eng.lib()
+    except eng.MripLibraryMissing:
+        from paper_1501_01405_gb300 import build
+        build.build()
+        eng.lib()
+    return eng
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mrip_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("mrip_create_model", "mrip_run", "mrip_stats", "mrip_destroy",
+                     "mrip_last_error", "mrip_mm1_simulate", "mrip_forest_fire_simulate",
+                     "mrip_walk_simulate", "mrip_tandem3_simulate", "mrip_stats_reduce",
+                     "mrip_mlp_loss_grad", "mrip_adam_step", "mrip_cv_reduce", "mrip_run_cv"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    eng = _engine()
+    out = subprocess.run(["nm", "-D", "--defined-only", eng.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if " T " in l)
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    # the binding declares a signature for each of them
+    from paper_1501_01405_gb300._abi import SIGNATURES
+    assert sorted(SIGNATURES) == _declared()
+
+
+@pytest.mark.parametrize("df", [1, 2, 3, 4, 9, 31, 127, 229, 255, 1023, 4095, 2**17 - 1])
+@pytest.mark.parametrize("conf", [0.9, 0.95, 0.99])
+def test_t_crit_matches_oracle(df, conf):
+    eng = _engine()
+    got = eng.mrip_t_crit(conf, df)
+    ref = oracle.t_crit(conf, df)
+    assert got == pytest.approx(ref, rel=2e-15)
+
+
+def test_stats_finalize_matches_oracle():
+    eng = _engine()
+    rng = np.random.default_rng(3)
+    rows = [rng.normal(5, 2, size=n) for n in (2, 3, 32, 256)]
+    nmm2 = []
+    for r in rows:
+        m = r.mean()
+        nmm2 += [len(r), m, float(((r - m) ** 2).sum())]
+    got = eng.mrip_stats_finalize(np.array(nmm2), 0.95)
+    for g, r in zip(got, rows):
+        ref = ostats.ci(r, 0.95)
+        assert g["n"] == ref["n"]
+        assert g["half_width"] == pytest.approx(ref["half_width"], rel=1e-13)
+        assert g["t_crit"] == pytest.approx(ref["t_crit"], rel=1e-14)
+    one = eng.mrip_stats_finalize(np.array([1.0, 7.0, 0.0]), 0.95)[0]
+    assert one["n"] == 1 and one["mean"] == 7.0 and np.isnan(one["half_width"])
+
+
+def test_invalid_arguments_rejected_on_host():
+    eng = _engine()
+    with pytest.raises(eng.MripError) as e:
+        eng.mrip_create_model(eng.MRIP_FOREST_FIRE, L=100, n_steps=10, density=0.5, window=5)
+    assert e.value.code == 1
+    with pytest.raises(eng.MripError):
+        eng.mrip_create_model(eng.MRIP_MM1, n_clients=0)
+    with pytest.raises(eng.MripError):
+        eng.mrip_create_model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 40)
+    with pytest.raises(eng.MripError):
+        eng.mrip_t_crit(1.5, 3)
+    L = eng.lib()
+    # stage entry points validate sizes before touching the device
+    assert L.mrip_mm1_simulate(None, -1, 1, 1, 0, 0, None, None, None, None) == 1
+    assert L.mrip_forest_fire_simulate(None, 1, 1, 100, 10, 0.5, 0, None, None, None, None,
+                                       None) == 1
+    r = (ctypes.c_double * 1)(2.5)
+    assert L.mrip_walk_simulate(r, 1, 4, 0, 100, 0, 0, 0, 0, ctypes.c_void_p(16), None) == 1
+    assert b"integer" in L.mrip_last_error()
+
+
+def test_plan_json_round_trip_and_rejection():
+    eng = _engine()
+    m = eng.Model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 30)
+    m.set_plan('{"mapping": 5, "warps_per_cta": 8, "ctas_per_sm": 2, "chunk": 64}')
+    assert m.get_plan() == '{"mapping": 5, "warps_per_cta": 8, "ctas_per_sm": 2, "chunk": 64}'
+    with pytest.raises(eng.MripError):
+        m.set_plan('{"mapping": 5, "bogus": 1}')
+    with pytest.raises(eng.MripError):
+        m.set_plan('{"mapping": 4}')  # CTA mapping is for lattices
+    q = eng.Model(eng.MRIP_MM1, n_clients=10)
+    with pytest.raises(eng.MripError):
+        q.stats()
+    m.close()
+    q.close()

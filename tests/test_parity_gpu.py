@@ -1,0 +1,403 @@
+"""GPU parity: every stage of the CUDA path against the oracle, through the C ABI.
+
+Integer and lattice outputs must match bit for bit; FP64 outputs within
+1e-12 relative (the engine's log may differ from the C library's by an ulp,
+and a warp-cooperative replay sums in another order).  Sizes span several
+tiles with ragged tails; the full-size workloads run on the GPU in the
+launch configuration the bench uses and are checked on sampled replications.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import mrip_inputs
+import oracle
+import oracle.stats as ostats
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available(), "GPU parity tests need CUDA"
+    import paper_1501_01405_gb300 as e
+    e.lib()  # fails loudly if the engine was not built
+    return e
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def dev(torch, a, dtype=None):
+    return torch.tensor(np.asarray(a), dtype=dtype, device="cuda")
+
+
+def threads():
+    return oracle.host_threads()
+
+
+# ------------------------------------------------------------------ streams
+def test_philox_bit_exact(eng, torch_mod):
+    t = torch_mod
+    rng = np.random.default_rng(1)
+    n = (1 << 16) + 17
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+    out = t.empty((n, 4), dtype=t.int32, device="cuda")
+    eng.mrip_philox(dev(t, ctr.view(np.int32)), dev(t, key.view(np.int32)), out)
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.philox4x32_10(ctr, key))
+
+
+def test_expo_variates(eng, torch_mod):
+    t = torch_mod
+    rng = np.random.default_rng(2)
+    n = 100003
+    lo = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    hi = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+    lo[:2], hi[:2] = [0, 0xFFFFFFFF], [0, 0xFFFFFFFF]
+    rate = rng.uniform(0.3, 3.0, n)
+    u = t.empty(n, dtype=t.float64, device="cuda")
+    e = t.empty(n, dtype=t.float64, device="cuda")
+    eng.mrip_expo(dev(t, lo.view(np.int32)), dev(t, hi.view(np.int32)), dev(t, rate), u, e)
+    u_ref, e_ref = oracle.u53_expo(lo, hi, rate)
+    assert np.array_equal(u.cpu().numpy(), u_ref)
+    np.testing.assert_allclose(e.cpu().numpy(), e_ref, rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------------------ M/M/1
+MM1_DPS = np.array([[0.9, 1.0], [0.5, 1.0], [1.2, 1.0]])
+
+
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP"])
+@pytest.mark.parametrize("n_clients", [1, 31, 1000, 1337])
+def test_mm1_all_mappings(eng, torch_mod, mapping, n_clients):
+    t = torch_mod
+    n_reps = 37
+    items = oracle.all_items(3, n_reps)
+    out = [t.empty(3 * n_reps, dtype=t.float64, device="cuda") for _ in range(3)]
+    eng.mrip_mm1_simulate(dev(t, MM1_DPS), n_reps, n_clients, 42,
+                          getattr(eng, "MRIP_MAP_" + mapping), *out)
+    ref = oracle.mm1(MM1_DPS, *items, n_clients, 42, threads=threads())
+    for g, r in zip(out, ref):
+        np.testing.assert_allclose(g.cpu().numpy(), r, rtol=REL, atol=1e-300)
+
+
+def test_mm1_workload_full(eng, torch_mod):
+    """32 replications x 1,000 clients, lambda 0.9, mu 1, seed 42: every value."""
+    t = torch_mod
+    w = mrip_inputs.workload("mm1_32")
+    wait = t.empty(w["n_reps"], dtype=t.float64, device="cuda")
+    eng.mrip_mm1_simulate(dev(t, w["dps"]), w["n_reps"], w["n_clients"], w["seed"],
+                          eng.MRIP_MAP_WARP_COOP, wait)
+    ref, _, _ = oracle.mm1(w["dps"], *oracle.all_items(1, w["n_reps"]), w["n_clients"], w["seed"])
+    np.testing.assert_allclose(wait.cpu().numpy(), ref, rtol=REL)
+    c = ostats.ci(ref, 0.95)
+    m = eng.Model(eng.MRIP_MM1, n_clients=w["n_clients"])
+    m.set_plan('{"mapping": 3}')
+    m.run(w["dps"], w["n_reps"], w["seed"])
+    s = m.stats(0.95)[0]
+    assert s["n"] == 32
+    assert s["mean"] == pytest.approx(c["mean"], rel=REL)
+    assert s["half_width"] == pytest.approx(c["half_width"], rel=REL)
+
+
+# ------------------------------------------------------------------ tandem
+def test_tandem_thread_and_wlp(eng, torch_mod):
+    t = torch_mod
+    dps = mrip_inputs.tandem_design_points(5, seed=3)
+    n_reps, n_clients, window = 7, 2000, 100
+    ref_y, ref_f = oracle.tandem3(dps, *oracle.all_items(5, n_reps), n_clients, 42,
+                                  window=window, threads=threads())
+    for mapping in (eng.MRIP_MAP_THREAD, eng.MRIP_MAP_WARP_1LANE):
+        y = t.empty(5 * n_reps, dtype=t.float64, device="cuda")
+        f = t.empty(8 * 5 * n_reps, dtype=t.float64, device="cuda")
+        eng.mrip_tandem3_simulate(dev(t, dps), 0, n_reps, n_clients, window, 42, 0, mapping, y, f)
+        np.testing.assert_allclose(y.cpu().numpy(), ref_y, rtol=REL)
+        np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, ref_f, rtol=REL)
+
+
+def test_tandem_offset_tag_and_short_runs(eng, torch_mod):
+    t = torch_mod
+    dps = mrip_inputs.tandem_design_points(3, seed=4)
+    # control runs: tag 2, replications 5..13, only the early window simulated
+    y = t.empty(3 * 9, dtype=t.float64, device="cuda")
+    f = t.empty(8 * 3 * 9, dtype=t.float64, device="cuda")
+    eng.mrip_tandem3_simulate(dev(t, dps), 5, 9, 100, 100, 42, 2, eng.MRIP_MAP_THREAD, y, f)
+    dp, rep = oracle.all_items(3, 9)
+    ry, rf = oracle.tandem3(dps, dp, rep + 5, 100, 42, window=100, tag=2)
+    np.testing.assert_allclose(y.cpu().numpy(), ry, rtol=REL)
+    np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
+    # fewer clients than the window
+    eng.mrip_tandem3_simulate(dev(t, dps), 0, 9, 7, 100, 42, 0, eng.MRIP_MAP_THREAD, y, f)
+    ry, rf = oracle.tandem3(dps, *oracle.all_items(3, 9), 7, 42, window=100)
+    np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
+
+
+def test_tandem_workload_full_sampled(eng, torch_mod):
+    """4,096 design points x 256 replications x 10,000 clients on the GPU;
+    96 sampled replications against the oracle."""
+    t = torch_mod
+    w = mrip_inputs.workload("tandem_cv")
+    n = w["n_dp"] * w["n_reps"]
+    y = t.empty(n, dtype=t.float64, device="cuda")
+    f = t.empty(8 * n, dtype=t.float64, device="cuda")
+    eng.mrip_tandem3_simulate(dev(t, w["dps"]), 0, w["n_reps"], w["n_clients"], w["window"],
+                              w["seed"], 0, eng.MRIP_MAP_THREAD, y, f)
+    rng = np.random.default_rng(9)
+    pick = np.concatenate([[0, n - 1, 255, 256], rng.choice(n, 92, replace=False)])
+    dp, rep = pick // w["n_reps"], pick % w["n_reps"]
+    ry, rf = oracle.tandem3(w["dps"], dp, rep, w["n_clients"], w["seed"], window=w["window"],
+                            threads=threads())
+    gy = y.cpu().numpy()[pick]
+    gf = f.cpu().numpy().reshape(8, -1)[:, pick].T
+    np.testing.assert_allclose(gy, ry, rtol=REL)
+    np.testing.assert_allclose(gf, rf, rtol=REL)
+
+
+# ------------------------------------------------------------------ forest fire
+@pytest.mark.parametrize("L", [32, 64, 128, 256])
+@pytest.mark.parametrize("n_steps", [1, 64, 130])
+def test_forest_fire_bit_exact(eng, torch_mod, L, n_steps):
+    t = torch_mod
+    dps = np.array([[0.05, 0.002], [0.3, 0.05]])
+    n_reps = 3
+    items = 2 * n_reps
+    counts = t.empty(items * n_steps, dtype=t.int32, device="cuda")
+    scalar = t.empty(items, dtype=t.float64, device="cuda")
+    final = t.empty(items * L * L, dtype=t.uint8, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, dps), n_reps, L, n_steps, 0.5, 42, None, counts,
+                                  scalar, final)
+    gc = counts.cpu().numpy().reshape(items, n_steps)
+    gs = final.cpu().numpy().reshape(items, L, L)
+    gsc = scalar.cpu().numpy()
+    for i, (d, r) in enumerate(zip(*oracle.all_items(2, n_reps))):
+        rc, rs = oracle.forest_fire_rep(L, n_steps, dps[d, 0], dps[d, 1], 0.5, 42, d, r)
+        assert np.array_equal(gc[i], rc)
+        assert np.array_equal(gs[i], rs)
+        assert gsc[i] == rc.sum() / (n_steps * L * L)
+
+
+def test_forest_fire_from_given_states(eng, torch_mod):
+    t = torch_mod
+    L, n_steps, n_reps = 64, 70, 4
+    rng = np.random.default_rng(5)
+    init = rng.integers(0, 3, size=(n_reps, L, L)).astype(np.uint8)
+    init[0] = 1
+    init[0, 10, 10] = 2  # single fire front on a full forest
+    dps = np.array([[0.0, 0.0]])
+    counts = t.empty(n_reps * n_steps, dtype=t.int32, device="cuda")
+    final = t.empty(n_reps * L * L, dtype=t.uint8, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, dps), n_reps, L, n_steps, 0.5, 7, dev(t, init), counts,
+                                  None, final)
+    gc = counts.cpu().numpy().reshape(n_reps, n_steps)
+    for r in range(n_reps):
+        rc, rs = oracle.forest_fire_rep(L, n_steps, 0.0, 0.0, 0.5, 7, 0, r, init_state=init[r])
+        assert np.array_equal(gc[r], rc)
+        assert np.array_equal(final.cpu().numpy().reshape(n_reps, L, L)[r], rs)
+    assert gc[0, :31].tolist() == [4 * k for k in range(1, 32)]
+
+
+def test_forest_fire_zero_steps_is_initial_state(eng, torch_mod):
+    t = torch_mod
+    L = 128
+    final = t.empty(2 * L * L, dtype=t.uint8, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, [[0.01, 1e-5]]), 2, L, 0, 0.37, 42, None, None, None,
+                                  final)
+    for r in range(2):
+        _, rs = oracle.forest_fire_rep(L, 0, 0.01, 1e-5, 0.37, 42, 0, r)
+        assert np.array_equal(final.cpu().numpy().reshape(2, L, L)[r], rs)
+
+
+def test_forest_fire_workload_full_sampled(eng, torch_mod):
+    """128x128, 1,000 steps, 1,024 replications on the GPU; four replications
+    (first, last, two inside) bit-exact against the oracle."""
+    t = torch_mod
+    w = mrip_inputs.workload("ff128")
+    counts = t.empty(w["n_reps"] * w["n_steps"], dtype=t.int32, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], w["n_steps"],
+                                  w["density"], w["seed"], None, counts)
+    gc = counts.cpu().numpy().reshape(w["n_reps"], w["n_steps"])
+    pick = np.array([0, 1, 511, 1023])
+    rc = oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"],
+                            np.zeros(4, np.int32), pick, w["seed"], threads=threads())
+    assert np.array_equal(gc[pick], rc)
+    assert gc.min() >= 0 and gc.max() <= w["L"] ** 2
+
+
+def test_forest_fire_cv_workload_sampled(eng, torch_mod):
+    """256x256, 2,000 steps, 64 design points x 128 replications on the GPU;
+    replications {0, 127} of design points {0, 21, 42, 63} against the oracle."""
+    t = torch_mod
+    w = mrip_inputs.workload("ff256_cv")
+    n = w["n_dp"] * w["n_reps"]
+    counts = t.empty(n * w["n_steps"], dtype=t.int32, device="cuda")
+    scalar = t.empty(n, dtype=t.float64, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], w["n_steps"],
+                                  w["density"], w["seed"], None, counts, scalar)
+    gc = counts.cpu().numpy().reshape(n, w["n_steps"])
+    dp = np.repeat([0, 21, 42, 63], 2).astype(np.int32)
+    rep = np.tile([0, 127], 4)
+    rc = oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"], dp, rep, w["seed"],
+                            threads=threads())
+    idx = dp * w["n_reps"] + rep
+    assert np.array_equal(gc[idx], rc)
+    sc = scalar.cpu().numpy()[idx]
+    assert np.array_equal(sc, rc.sum(axis=1) / (w["n_steps"] * w["L"] ** 2))
+
+
+# ------------------------------------------------------------------ walk
+WALK_MAPS = ["PERSISTENT", "THREAD", "WARP_1LANE", "WARP_COOP"]
+
+
+@pytest.mark.parametrize("mapping", WALK_MAPS)
+def test_walk_all_mappings_bit_exact(eng, torch_mod, mapping):
+    t = torch_mod
+    radii = [1.0, 2.0, 3.0, 16.0, 33.0, 5.0]
+    n_reps = 301
+    tau = t.empty(len(radii) * n_reps, dtype=t.int64, device="cuda")
+    eng.mrip_walk_simulate(radii, n_reps, 42, 1 << 38, getattr(eng, "MRIP_MAP_" + mapping), tau,
+                           warps_per_cta=4, ctas_per_sm=2, chunk=37)
+    t.cuda.synchronize()
+    eng.mrip_check_device_flags()
+    ref = oracle.walk(radii, *oracle.all_items(len(radii), n_reps), 42, threads=threads())
+    assert np.array_equal(tau.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("mapping", WALK_MAPS)
+def test_walk_step_cap_reported(eng, torch_mod, mapping):
+    t = torch_mod
+    tau = t.empty(2 * 40, dtype=t.int64, device="cuda")
+    eng.mrip_walk_simulate([200.0, 2.0], 40, 42, 100, getattr(eng, "MRIP_MAP_" + mapping), tau)
+    t.cuda.synchronize()
+    with pytest.raises(eng.MripError) as e:
+        eng.mrip_check_device_flags()
+    assert e.value.code == 4
+    got = tau.cpu().numpy()
+    ref = oracle.walk([200.0, 2.0], *oracle.all_items(2, 40), 42, max_steps=100)
+    assert np.array_equal(got, ref) and np.all(got[:40] == -1)
+    eng.mrip_check_device_flags()  # the flag was cleared
+
+
+def test_walk_workload_full_sampled(eng, torch_mod):
+    """8 radii x 2^17 replications, persistent work stealing; 1,600 sampled
+    replications bit-exact, every tau has the parity of R."""
+    t = torch_mod
+    w = mrip_inputs.workload("walk8")
+    radii = w["dps"][:, 0]
+    n = len(radii) * w["n_reps"]
+    tau = t.empty(n, dtype=t.int64, device="cuda")
+    eng.mrip_walk_simulate(radii, w["n_reps"], w["seed"], 1 << 38, eng.MRIP_MAP_PERSISTENT, tau)
+    t.cuda.synchronize()
+    eng.mrip_check_device_flags()
+    g = tau.cpu().numpy()
+    dp = np.repeat(np.arange(len(radii)), w["n_reps"])
+    assert np.all(g % 2 == radii[dp].astype(np.int64) % 2) and np.all(g >= radii[dp])
+    rng = np.random.default_rng(11)
+    pick = np.concatenate([np.arange(8) * w["n_reps"], rng.choice(n, 1592, replace=False)])
+    ref = oracle.walk(radii, pick // w["n_reps"], pick % w["n_reps"], w["seed"], threads=threads())
+    assert np.array_equal(g[pick], ref)
+
+
+# ------------------------------------------------------------------ statistics
+@pytest.mark.parametrize("n_reps", [1, 2, 255, 257, 1 << 17])
+def test_stats_reduce(eng, torch_mod, n_reps):
+    t = torch_mod
+    n_dp = 5
+    x = mrip_inputs.random_matrix((n_dp, n_reps), 3, scale=2.0, loc=7.0)
+    out = t.empty(n_dp * 3, dtype=t.float64, device="cuda")
+    eng.mrip_stats_reduce(dev(t, x), out)
+    got = out.cpu().numpy().reshape(n_dp, 3)
+    for d in range(n_dp):
+        n, mean, var = ostats.dp_stats(x[d])
+        assert got[d, 0] == n
+        assert got[d, 1] == pytest.approx(mean, rel=1e-13)
+        if n > 1:
+            assert got[d, 2] / (n - 1) == pytest.approx(var, rel=1e-12)
+        else:
+            assert got[d, 2] == 0.0
+
+
+# ------------------------------------------------------------------ model handles
+def test_handles_match_oracle_intervals(eng, torch_mod):
+    # forest fire, 2 design points x 20 replications
+    m = eng.Model(eng.MRIP_FOREST_FIRE, L=64, n_steps=120, density=0.5, window=25)
+    dps = np.array([[0.02, 0.001], [0.2, 0.0001]])
+    m.run(dps, 20, 9)
+    st = m.stats(0.95)
+    counts = m.outputs(0, np.int32).reshape(40, 120)
+    rc = oracle.forest_fire(64, 120, dps, 0.5, *oracle.all_items(2, 20), 9, threads=threads())
+    assert np.array_equal(counts, rc)
+    y = rc.sum(axis=1) / (120 * 64 * 64)
+    for d in range(2):
+        c = ostats.ci(y[d * 20:(d + 1) * 20])
+        assert st[d]["mean"] == pytest.approx(c["mean"], rel=REL)
+        assert st[d]["half_width"] == pytest.approx(c["half_width"], rel=REL)
+    m.close()
+    # walk, plans and a second run of the same graph with a new seed
+    wm = eng.Model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 38)
+    radii = np.array([[12.0], [7.0], [20.0]])
+    for plan in ('{"mapping": 5, "warps_per_cta": 4, "ctas_per_sm": 1, "chunk": 16}',
+                 '{"mapping": 1}', '{"mapping": 3}'):
+        for seed in (1, 2):
+            wm.set_plan(plan)
+            wm.run(radii, 100, seed)
+            st = wm.stats(0.95)
+            tau = wm.outputs(0, np.int64)
+            ref = oracle.walk(radii[:, 0], *oracle.all_items(3, 100), seed)
+            assert np.array_equal(tau, ref)
+            for d in range(3):
+                c = ostats.ci(ref[d * 100:(d + 1) * 100].astype(np.float64))
+                assert st[d]["mean"] == pytest.approx(c["mean"], rel=REL)
+                assert st[d]["half_width"] == pytest.approx(c["half_width"], rel=REL)
+    wm.close()
+    # tandem and M/M/1 handles
+    tm = eng.Model(eng.MRIP_TANDEM3, n_clients=500, window=50)
+    tdp = mrip_inputs.tandem_design_points(4, seed=8)
+    tm.run(tdp, 9, 5)
+    ty = tm.outputs(0).reshape(4, 9)
+    ry, _ = oracle.tandem3(tdp, *oracle.all_items(4, 9), 500, 5, window=50)
+    np.testing.assert_allclose(ty.reshape(-1), ry, rtol=REL)
+    tm.close()
+
+
+def test_autotune_keeps_results_and_picks_a_plan(eng, torch_mod, tmp_path):
+    wm = eng.Model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 38)
+    radii = np.array([[64.0], [16.0], [32.0]])
+    cache = str(tmp_path / "plans.jsonl")
+    wm.autotune(radii, 2000, 3, trials=1, cache_path=cache)
+    plan = wm.get_plan()
+    assert '"mapping"' in plan
+    text = open(cache).read()
+    assert text.count("\n") == 1
+    # cached: a second autotune reads the file and times nothing
+    wm2 = eng.Model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 38)
+    wm2.autotune(radii, 2000, 3, trials=1, cache_path=cache)
+    assert wm2.get_plan() == plan
+    assert open(cache).read().count("\n") == 1
+    wm2.run(radii, 2000, 3)
+    ref = oracle.walk(radii[:, 0], *oracle.all_items(3, 2000), 3, threads=threads())
+    assert np.array_equal(wm2.outputs(0, np.int64), ref)
+    wm.close()
+    wm2.close()
+
+
+def test_errors_do_not_poison_the_context(eng, torch_mod):
+    t = torch_mod
+    with pytest.raises(eng.MripError):
+        eng.mrip_mm1_simulate(dev(t, MM1_DPS), 2, 0, 42, eng.MRIP_MAP_THREAD,
+                              t.empty(6, dtype=t.float64, device="cuda"))
+    m = eng.Model(eng.MRIP_MM1, n_clients=10)
+    with pytest.raises(eng.MripError):
+        m.run(np.array([[0.5, -1.0]]), 4, 1)
+    m.run(np.array([[0.5, 1.0]]), 4, 1)
+    assert m.stats()[0]["n"] == 4
+    m.close()
