@@ -1,0 +1,549 @@
+#!/usr/bin/env python
+"""Benchmark of the MRIP engine: one JSON line on stdout (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl engine|reference]
+
+A step is one pass of the hot path over one batch of synthetic input: all
+replications of the workload simulated by the CUDA kernels and reduced to
+per-design-point (n, mean, M2) on the device.  The default workload is the
+128x128 forest fire (1,024 replications x 1,000 steps); the others are
+selectable (mm1_32, walk8, tandem, ff256, tandem_cv).
+
+value   = replications / s over the K timed steps, inputs resident in HBM,
+          device time from CUDA events on the launching stream, L2 flushed
+          (256 MiB write) between steps outside the timed intervals.
+e2e     = the same through the public model-handle API (mrip_run with host
+          design points + mrip_stats reading the intervals back), wall time.
+roofline= the dominant kernel's algorithmic work per launch / its mean event
+          time, against the peak derived in the design doc.
+cpu_baseline = the oracle (plain C) on a bounded sample of the same workload
+          on all host cores (rank 0, N = 1 only).
+
+With --impl reference the oracle itself is timed as the reference arm.
+Under torchrun (N > 1) every rank runs its own batch (seed + rank: weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mrip_inputs  # noqa: E402
+
+METRIC = ("replications/sec and time to target 95% CI half-width, plain vs control-variate")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Nominal unit counts (per SM per clock) used for the ALU rooflines.
+SMS = 152
+SM_MAX_MHZ = 2070.0
+IMUL_PER_CLK_SM = 64      # 32-bit integer multiply / multiply-add results
+DFMA_PER_CLK_SM = 2       # FP64 fused multiply-add results (1.25 TFLOP/s nominal)
+INT_MULS_PER_PHILOX = 40  # 10 rounds x 2 products x (low + high half)
+
+
+def imul_peak_gops():
+    return SMS * IMUL_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+
+
+# ---------------------------------------------------------------------------
+# workloads: device state, one step, the dominant kernel, the oracle sample
+# ---------------------------------------------------------------------------
+class Workload:
+    name = ""
+    units_name = "replications"
+    dtype = ""
+
+    def __init__(self, rank):
+        self.rank = rank
+
+    def config(self):
+        raise NotImplementedError
+
+
+class ForestFire(Workload):
+    dtype = "u32"
+
+    def __init__(self, rank, key="ff128"):
+        super().__init__(rank)
+        self.key = key
+        self.w = mrip_inputs.workload(key)
+        self.name = key
+        self.seed = self.w["seed"] + rank
+
+    def units(self):
+        return self.w["n_dp"] * self.w["n_reps"]
+
+    def config(self):
+        w = self.w
+        return {"workload": "%s: forest fire %dx%d, %d steps, %d design point(s) x %d "
+                            "replications, density %.2f" % (self.key, w["L"], w["L"], w["n_steps"],
+                                                             w["n_dp"], w["n_reps"], w["density"]),
+                "L": w["L"], "n_steps": w["n_steps"], "n_dp": w["n_dp"], "n_reps": w["n_reps"],
+                "p_grow": float(w["dps"][0, 0]), "p_lightning": float(w["dps"][0, 1]),
+                "seed": self.seed, "mapping": "CTA per replication, bit-packed rows"}
+
+    def setup(self, eng, torch):
+        w = self.w
+        self.eng, self.torch = eng, torch
+        self.d_dps = torch.tensor(w["dps"], dtype=torch.float64, device="cuda")
+        n = self.units()
+        self.counts = torch.empty(n * w["n_steps"], dtype=torch.int32, device="cuda")
+        self.scalar = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.nmm2 = torch.empty(w["n_dp"] * 3, dtype=torch.float64, device="cuda")
+
+    def step(self, k_start=None, k_end=None):
+        w = self.w
+        if k_start is not None:
+            k_start.record()
+        self.eng.mrip_forest_fire_simulate(self.d_dps, w["n_reps"], w["L"], w["n_steps"],
+                                           w["density"], self.seed, None, self.counts,
+                                           self.scalar)
+        if k_end is not None:
+            k_end.record()
+        self.eng.mrip_stats_reduce(self.scalar.view(w["n_dp"], w["n_reps"]), self.nmm2)
+
+    launches_per_step = 2
+
+    def roofline_work(self):
+        w = self.w
+        cells = w["L"] * w["L"] * w["n_steps"] * self.units()
+        return dict(kernel="forest_fire_kernel<%d>" % (w["L"] // 32), bound="alu",
+                    unit="Gop/s (32-bit integer multiply)",
+                    work=cells * INT_MULS_PER_PHILOX / 4.0, peak=imul_peak_gops(),
+                    peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
+                        SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
+                    per_unit="10 int multiplies per cell-update (1/4 Philox block)")
+
+    def make_model(self):
+        w = self.w
+        m = self.eng.Model(self.eng.MRIP_FOREST_FIRE, L=w["L"], n_steps=w["n_steps"],
+                           density=w["density"], window=min(100, w["n_steps"]))
+        return m
+
+    def e2e_inputs(self):
+        return self.w["dps"], self.w["n_reps"]
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        w = self.w
+        rep = np.arange(n_items) % w["n_reps"]
+        dp = (np.arange(n_items) // w["n_reps"]) % w["n_dp"]
+        oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"], dp.astype(np.int32),
+                           rep, self.seed, threads=threads)
+
+
+class Walk(Workload):
+    dtype = "i32"
+
+    def __init__(self, rank):
+        super().__init__(rank)
+        self.w = mrip_inputs.workload("walk8")
+        self.name = "walk8"
+        self.seed = self.w["seed"] + rank
+        self.radii = self.w["dps"][:, 0].copy()
+
+    def units(self):
+        return self.w["n_dp"] * self.w["n_reps"]
+
+    def config(self):
+        w = self.w
+        return {"workload": "walk8: L1-exit walk, R in %s, %d replications each" % (
+            list(mrip_inputs.WALK_RADII), w["n_reps"]), "n_dp": w["n_dp"], "n_reps": w["n_reps"],
+                "seed": self.seed, "mapping": "persistent work stealing, lane refill"}
+
+    def setup(self, eng, torch):
+        self.eng, self.torch = eng, torch
+        n = self.units()
+        self.tau = torch.empty(n, dtype=torch.int64, device="cuda")
+
+    def step(self, k_start=None, k_end=None):
+        if k_start is not None:
+            k_start.record()
+        self.eng.mrip_walk_simulate(self.radii, self.w["n_reps"], self.seed, 1 << 38,
+                                    self.eng.MRIP_MAP_PERSISTENT, self.tau)
+        if k_end is not None:
+            k_end.record()
+
+    launches_per_step = 1
+
+    def roofline_work(self):
+        moves = 0.0
+        for R in mrip_inputs.WALK_RADII:
+            moves += self.w["n_reps"] * (2.0 / 3.0) * R * R
+        return dict(kernel="walk_persistent_kernel", bound="alu",
+                    unit="Gop/s (32-bit integer multiply)", work=moves / 64.0 * INT_MULS_PER_PHILOX,
+                    peak=imul_peak_gops(), peak_source="nominal int-mul rate",
+                    per_unit="40 int multiplies per 64 moves (one Philox block); E[tau] ~ 2R^2/3")
+
+    def make_model(self):
+        return self.eng.Model(self.eng.MRIP_WALK_L1_EXIT, max_steps=1 << 38)
+
+    def e2e_inputs(self):
+        return self.w["dps"], self.w["n_reps"]
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        w = self.w
+        g = np.arange(n_items)
+        dp = (g % w["n_dp"]).astype(np.int32)
+        rep = g // w["n_dp"]
+        oracle.walk(self.radii, dp, rep, self.seed, threads=threads)
+
+
+class Queue(Workload):
+    dtype = "f64"
+
+    def __init__(self, rank, key):
+        super().__init__(rank)
+        self.key = key
+        if key == "mm1_32":
+            self.w = mrip_inputs.workload("mm1_32")
+        else:
+            self.w = mrip_inputs.workload("tandem_cv")
+        self.name = key
+        self.seed = self.w["seed"] + rank
+
+    def units(self):
+        return self.w["n_dp"] * self.w["n_reps"]
+
+    def config(self):
+        w = self.w
+        if self.key == "mm1_32":
+            return {"workload": "mm1_32: M/M/1 Lindley, lambda 0.9, mu 1, 1000 clients, 32 "
+                                "replications", "n_reps": w["n_reps"], "n_clients": w["n_clients"],
+                    "seed": self.seed, "mapping": "warp-cooperative max-plus scan"}
+        return {"workload": "tandem: 3-station tandem, %d design points x %d replications x %d "
+                            "clients (plain estimator)" % (w["n_dp"], w["n_reps"], w["n_clients"]),
+                "n_dp": w["n_dp"], "n_reps": w["n_reps"], "n_clients": w["n_clients"],
+                "seed": self.seed, "mapping": "thread per replication"}
+
+    def setup(self, eng, torch):
+        self.eng, self.torch = eng, torch
+        w = self.w
+        n = self.units()
+        self.d_dps = torch.tensor(w["dps"], dtype=torch.float64, device="cuda")
+        self.y = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.feat = torch.empty(8 * n, dtype=torch.float64, device="cuda") \
+            if self.key != "mm1_32" else None
+        self.nmm2 = torch.empty(w["n_dp"] * 3, dtype=torch.float64, device="cuda")
+
+    def step(self, k_start=None, k_end=None):
+        w = self.w
+        if k_start is not None:
+            k_start.record()
+        if self.key == "mm1_32":
+            self.eng.mrip_mm1_simulate(self.d_dps, w["n_reps"], w["n_clients"], self.seed,
+                                       self.eng.MRIP_MAP_WARP_COOP, self.y)
+        else:
+            self.eng.mrip_tandem3_simulate(self.d_dps, 0, w["n_reps"], w["n_clients"],
+                                           w["window"], self.seed, 0, self.eng.MRIP_MAP_THREAD,
+                                           self.y, self.feat)
+        if k_end is not None:
+            k_end.record()
+        self.eng.mrip_stats_reduce(self.y.view(w["n_dp"], w["n_reps"]), self.nmm2)
+
+    launches_per_step = 2
+
+    def roofline_work(self):
+        w = self.w
+        clients = self.units() * w["n_clients"]
+        logs = 2 if self.key == "mm1_32" else 4
+        return dict(kernel="mm1_warp_coop_kernel" if self.key == "mm1_32"
+                    else "tandem3_serial_kernel", bound="alu",
+                    unit="G exponential variates/s", work=clients * logs,
+                    peak=None, peak_source="see DESIGN.md (FP64-pipe bound)",
+                    per_unit="%d exponential variates per client" % logs)
+
+    def make_model(self):
+        w = self.w
+        if self.key == "mm1_32":
+            m = self.eng.Model(self.eng.MRIP_MM1, n_clients=w["n_clients"])
+            m.set_plan('{"mapping": 3}')
+            return m
+        return self.eng.Model(self.eng.MRIP_TANDEM3, n_clients=w["n_clients"],
+                              window=w["window"])
+
+    def e2e_inputs(self):
+        return self.w["dps"], self.w["n_reps"]
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        w = self.w
+        g = np.arange(n_items)
+        dp = (g % w["n_dp"]).astype(np.int32)
+        rep = (g // w["n_dp"]) % w["n_reps"]
+        if self.key == "mm1_32":
+            oracle.mm1(w["dps"], dp, rep, w["n_clients"], self.seed, threads=threads)
+        else:
+            oracle.tandem3(w["dps"], dp, rep, w["n_clients"], self.seed, window=w["window"],
+                           threads=threads)
+
+
+def make_workload(name, rank):
+    if name in ("ff128", "ff256"):
+        return ForestFire(rank, "ff128" if name == "ff128" else "ff256_cv")
+    if name == "walk8":
+        return Walk(rank)
+    if name in ("mm1_32", "tandem"):
+        return Queue(rank, name)
+    raise SystemExit("unknown workload %s" % name)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def time_oracle(wl, target_s, threads):
+    """Run the oracle on a sample sized to about target_s seconds on `threads`
+    cores; returns (items, seconds)."""
+    import oracle
+    oracle.lib()
+    n = threads
+    t0 = time.perf_counter()
+    wl.oracle_sample(n, threads)
+    dt = time.perf_counter() - t0
+    while dt < 0.5 and n < 10**7:  # calibrate on cheap workloads
+        n *= 4
+        t0 = time.perf_counter()
+        wl.oracle_sample(n, threads)
+        dt = time.perf_counter() - t0
+    per_item = dt / n
+    m = max(threads, int(target_s / per_item) // threads * threads)
+    t0 = time.perf_counter()
+    wl.oracle_sample(m, threads)
+    return m, time.perf_counter() - t0
+
+
+def reference_arm(args, wl, rank, world):
+    import oracle
+    if rank != 0:
+        return
+    threads = oracle.host_threads()
+    oracle.lib()
+    # size each step so the whole run stays within about three minutes
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    n_cal = threads
+    t0 = time.perf_counter()
+    wl.oracle_sample(n_cal, threads)
+    dt = time.perf_counter() - t0
+    while dt < 0.3 and n_cal < 10**7:
+        n_cal *= 4
+        t0 = time.perf_counter()
+        wl.oracle_sample(n_cal, threads)
+        dt = time.perf_counter() - t0
+    m = max(threads, int(per_step / (dt / n_cal)) // threads * threads)
+    for _ in range(args.warmup):
+        wl.oracle_sample(m, threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        wl.oracle_sample(m, threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * len(times) / total
+    sample = "%d replications per step of %s (the workload has %d)" % (m, wl.name, wl.units())
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": "replications/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": wl.dtype, "data": "synthetic", "config": wl.config(),
+            "cpu_baseline": {"value": value, "unit": "replications/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "replications/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="ff128",
+                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem"])
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = make_workload(args.workload, rank)
+
+    if args.impl == "reference":
+        reference_arm(args, wl, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_1501_01405_gb300 as eng
+    eng.lib()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl.setup(eng, torch)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ke = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # outside the timed interval
+        starts[i].record(stream)
+        wl.step(ks[i], ke[i])
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    kern_ms = [s.elapsed_time(e) for s, e in zip(ks, ke)]
+    if world > 1:
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dev_ms = float(tt.item())
+    total_units = wl.units() * args.steps * world
+    value = total_units / (dev_ms / 1e3)
+
+    # ---- end to end through the model-handle API, host buffers
+    model = wl.make_model()
+    model.set_stream(stream)
+    dps, n_reps = wl.e2e_inputs()
+    for _ in range(3):
+        model.run(dps, n_reps, wl.seed)
+        model.stats(0.95)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        model.run(dps, n_reps, wl.seed)
+        model.stats(0.95)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": total_units / e2e_s, "unit": "replications/s",
+           "h2d_bytes_per_step": int(np.asarray(dps).nbytes),
+           "d2h_bytes_per_step": int(np.asarray(dps).shape[0] * 3 * 8)}
+    model.close()
+
+    # ---- roofline of the dominant kernel
+    rw = wl.roofline_work()
+    kmean = sum(kern_ms) / len(kern_ms)
+    achieved = rw["work"] / (kmean / 1e3) / 1e9
+    roof = {"bound": rw["bound"], "kernel": rw["kernel"], "achieved": achieved,
+            "peak": rw["peak"], "unit": rw["unit"],
+            "frac": (achieved / rw["peak"]) if rw["peak"] else None,
+            "traffic": None, "kernel_ms": kmean, "per_unit": rw["per_unit"],
+            "peak_source": rw["peak_source"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "replications/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": wl.dtype, "data": "synthetic (seeded Philox streams)",
+            "config": dict(wl.config(), l2="flushed between timed steps (256 MiB write)",
+                           parallelism="replicas x%d (independent seeds)" % world),
+            "roofline": roof, "e2e": e2e, "clocks": clk,
+            "gpu_launches": wl.launches_per_step * args.steps,
+            "wall_s": t_wall}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        threads = oracle.host_threads()
+        n, s = time_oracle(wl, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": n / s, "unit": "replications/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": "%d replications of %s in %.1f s" % (n, wl.name, s)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,17 +1,19 @@
 // Stochastic forest-fire cellular automaton (Drossel-Schwabl rules), one
-// replication per CTA.
+// replication per CTA, the lattice held in shared memory.
 //
 // Layout: the L x L lattice (L = 32 W) is two bit planes, "tree" and
-// "burning", one 32-bit word per 32 cells of a row (bit m of word j of row y
-// is cell x = 32 j + m).  Thread y owns row y in registers.  A cell's north
-// and south neighbours come from the adjacent lanes by warp shuffle; the
-// first and last row of each warp are exchanged through a double-buffered
-// shared-memory halo, so one barrier per step suffices.  East and west
-// neighbours are shifts within the row (periodic).  The random word of cell
-// i = y L + x at step t is word (i mod 4) of Philox block (c0 = i div 4,
-// c1 = t); a thread compares its 32 cells' words with the growth and
-// lightning thresholds and packs the results into two words, then the new
-// state of 32 cells is a handful of bitwise operations:
+// "burning", one 32-bit word per 32 cells of a row (bit m of word k =
+// y W + j is cell x = 32 j + m of row y).  Both planes are double-buffered
+// in shared memory (2 buffers x 2 planes x L W words = 16 L W bytes); a step reads buffer
+// (t-1) mod 2 and writes buffer t mod 2, so one barrier per step suffices.
+// Thread i of the CTA updates words i, i + blockDim, ...: the word's
+// north/south neighbours are the words W above and below (periodic), its
+// east/west neighbour bits are shifts with the carry bit from the adjacent
+// word of the same row.  The random word of cell i = y L + x at step t is
+// word (i mod 4) of Philox block (c0 = i div 4, c1 = t); for lattice word k
+// that is blocks c0 = 8k .. 8k+7.  A thread compares its 32 cells' words
+// with the growth and lightning thresholds and packs the results into two
+// words; the new state of 32 cells is then a few bitwise operations:
 //   ignite = burning neighbour | lightning,
 //   burning' = tree & ignite,
 //   tree'    = (tree & ~ignite) | (empty & grow).
@@ -25,94 +27,89 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Threads per CTA for a lattice of W words per row.
 template <int W>
-__global__ void __launch_bounds__(32 * W) forest_fire_kernel(
+constexpr int ff_threads() {
+    return W == 1 ? 32 : W == 2 ? 64 : W == 4 ? 128 : W == 8 ? 256 : 512;
+}
+
+template <int W>
+__global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
     const double* __restrict__ dps, long long n_reps, int n_steps, uint32_t t_dens,
     const __grid_constant__ RoundKeys rk, const uint8_t* __restrict__ init,
     int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
     constexpr int L = 32 * W;
-    constexpr int NWARP = W;  // L rows, 32 rows per warp
-    __shared__ uint32_t halo[2][2][NWARP][W];  // [state parity][first/last row][warp][word]
+    constexpr int NWORD = L * W;  // words per plane
+    constexpr int TPB = ff_threads<W>();
+    constexpr int NWARP = TPB / 32;
+    extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD]
     __shared__ int cnt[2][64];
     __shared__ long long red[NWARP];
 
-    const int y = threadIdx.x;
-    const int lane = y & 31;
-    const int warp = y >> 5;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const long long item = blockIdx.x;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(item % n_reps);
     const uint32_t t_grow = threshold32(dps[2 * dp]);
     const uint32_t t_light = threshold32(dps[2 * dp + 1]);
     const uint32_t c3 = stream_word(0u, dp);
-    const uint32_t row_c0 = static_cast<uint32_t>(y) * (L / 4);
 
-    uint32_t T[W], B[W];
     if (init) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(
-            init + item * static_cast<long long>(L) * L + static_cast<long long>(y) * L);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(init + item * static_cast<long long>(L) * L);
+        for (int k = threadIdx.x; k < NWORD; k += TPB) {
             uint32_t tw = 0, bw = 0;
             for (int r = 0; r < 8; ++r) {
-                const uint32_t v = src[8 * j + r];
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t s = (v >> (8 * k)) & 0xFFu;
-                    tw |= (s == 1u ? 1u : 0u) << (4 * r + k);
-                    bw |= (s == 2u ? 1u : 0u) << (4 * r + k);
+                const uint32_t v = src[8 * k + r];
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t s = (v >> (8 * q)) & 0xFFu;
+                    tw |= (s == 1u ? 1u : 0u) << (4 * r + q);
+                    bw |= (s == 2u ? 1u : 0u) << (4 * r + q);
                 }
             }
-            T[j] = tw;
-            B[j] = bw;
+            lattice[k] = tw;
+            lattice[NWORD + k] = bw;
         }
     } else {
         const uint32_t c3i = stream_word(1u, dp);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
+        for (int k = threadIdx.x; k < NWORD; k += TPB) {
             uint32_t tw = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const uint4 b = philox(row_c0 + 8 * j + q, 0u, rep, c3i, rk);
+                const uint4 b = philox(8u * k + q, 0u, rep, c3i, rk);
                 tw |= (b.x < t_dens) ? (1u << (4 * q)) : 0u;
                 tw |= (b.y < t_dens) ? (1u << (4 * q + 1)) : 0u;
                 tw |= (b.z < t_dens) ? (1u << (4 * q + 2)) : 0u;
                 tw |= (b.w < t_dens) ? (1u << (4 * q + 3)) : 0u;
             }
-            T[j] = tw;
-            B[j] = 0u;
+            lattice[k] = tw;
+            lattice[NWORD + k] = 0u;
         }
     }
-    for (int i = threadIdx.x; i < 128; i += blockDim.x) (&cnt[0][0])[i] = 0;
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < W; ++j) halo[0][0][warp][j] = B[j];
-    }
-    if (lane == 31) {
-#pragma unroll
-        for (int j = 0; j < W; ++j) halo[0][1][warp][j] = B[j];
-    }
+    for (int i = threadIdx.x; i < 128; i += TPB) (&cnt[0][0])[i] = 0;
     __syncthreads();
 
-    const int wprev = (warp + NWARP - 1) % NWARP;
-    const int wnext = (warp + 1) % NWARP;
     long long my_sum = 0;
     for (int t = 1; t <= n_steps; ++t) {
-        const int rp = (t - 1) & 1;
-        uint32_t TN[W], BN[W];
+        const uint32_t* cur_t = lattice + ((t - 1) & 1) * 2 * NWORD;
+        const uint32_t* cur_b = cur_t + NWORD;
+        uint32_t* nxt_t = lattice + (t & 1) * 2 * NWORD;
+        uint32_t* nxt_b = nxt_t + NWORD;
         int c = 0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            uint32_t up = __shfl_up_sync(kFull, B[j], 1);
-            uint32_t dn = __shfl_down_sync(kFull, B[j], 1);
-            if (lane == 0) up = halo[rp][1][wprev][j];
-            if (lane == 31) dn = halo[rp][0][wnext][j];
-            const uint32_t west = (B[j] << 1) | (B[(j + W - 1) % W] >> 31);
-            const uint32_t east = (B[j] >> 1) | (B[(j + 1) % W] << 31);
-            const uint32_t nb = up | dn | west | east;
+        for (int k = threadIdx.x; k < NWORD; k += TPB) {
+            const int y = k / W;
+            const int j = k - y * W;
+            const uint32_t tw = cur_t[k];
+            const uint32_t bw = cur_b[k];
+            const uint32_t up = cur_b[((y + L - 1) & (L - 1)) * W + j];
+            const uint32_t dn = cur_b[((y + 1) & (L - 1)) * W + j];
+            const uint32_t bwest = cur_b[y * W + ((j + W - 1) & (W - 1))];
+            const uint32_t beast = cur_b[y * W + ((j + 1) & (W - 1))];
+            const uint32_t nb = up | dn | (bw << 1) | (bwest >> 31) | (bw >> 1) | (beast << 31);
             uint32_t g = 0, l = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const uint4 b = philox(row_c0 + 8 * j + q, static_cast<uint32_t>(t), rep, c3, rk);
+                const uint4 b = philox(8u * k + q, static_cast<uint32_t>(t), rep, c3, rk);
                 g |= (b.x < t_grow) ? (1u << (4 * q)) : 0u;
                 g |= (b.y < t_grow) ? (1u << (4 * q + 1)) : 0u;
                 g |= (b.z < t_grow) ? (1u << (4 * q + 2)) : 0u;
@@ -123,30 +120,18 @@ __global__ void __launch_bounds__(32 * W) forest_fire_kernel(
                 l |= (b.w < t_light) ? (1u << (4 * q + 3)) : 0u;
             }
             const uint32_t ignite = nb | l;
-            BN[j] = T[j] & ignite;
-            TN[j] = (T[j] & ~ignite) | (~(T[j] | B[j]) & g);
-            c += __popc(BN[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            T[j] = TN[j];
-            B[j] = BN[j];
+            const uint32_t nbw = tw & ignite;
+            nxt_b[k] = nbw;
+            nxt_t[k] = (tw & ~ignite) | (~(tw | bw) & g);
+            c += __popc(nbw);
         }
         c = __reduce_add_sync(kFull, c);
         if (lane == 0) atomicAdd(&cnt[((t - 1) >> 6) & 1][(t - 1) & 63], c);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < W; ++j) halo[t & 1][0][warp][j] = B[j];
-        }
-        if (lane == 31) {
-#pragma unroll
-            for (int j = 0; j < W; ++j) halo[t & 1][1][warp][j] = B[j];
-        }
         __syncthreads();
         if ((t & 63) == 0 || t == n_steps) {
             const int chunk = (t - 1) >> 6;
             const int n_slot = t - chunk * 64;
-            for (int s = threadIdx.x; s < n_slot; s += blockDim.x) {
+            for (int s = threadIdx.x; s < n_slot; s += TPB) {
                 const int v = cnt[chunk & 1][s];
                 cnt[chunk & 1][s] = 0;
                 my_sum += v;
@@ -169,29 +154,38 @@ __global__ void __launch_bounds__(32 * W) forest_fire_kernel(
         }
     }
     if (final_state) {
-        uint32_t* dst = reinterpret_cast<uint32_t*>(
-            final_state + item * static_cast<long long>(L) * L + static_cast<long long>(y) * L);
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
+        const uint32_t* fin_t = lattice + (n_steps & 1) * 2 * NWORD;
+        const uint32_t* fin_b = fin_t + NWORD;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(final_state + item * static_cast<long long>(L) * L);
+        for (int k = threadIdx.x; k < NWORD; k += TPB) {
+            const uint32_t tw = fin_t[k], bw = fin_b[k];
             for (int r = 0; r < 8; ++r) {
                 uint32_t v = 0;
-                for (int k = 0; k < 4; ++k) {
-                    const int m = 4 * r + k;
-                    const uint32_t s = ((T[j] >> m) & 1u) ? 1u : (((B[j] >> m) & 1u) ? 2u : 0u);
-                    v |= s << (8 * k);
+                for (int q = 0; q < 4; ++q) {
+                    const int m = 4 * r + q;
+                    const uint32_t s = ((tw >> m) & 1u) ? 1u : (((bw >> m) & 1u) ? 2u : 0u);
+                    v |= s << (8 * q);
                 }
-                dst[8 * j + r] = v;
+                dst[8 * k + r] = v;
             }
         }
     }
 }
 
 template <int W>
-void launch_ff(const double* dps, long long n_items, long long n_reps, int n_steps, uint32_t t_dens,
-               const RoundKeys& rk, const uint8_t* init, int32_t* counts, double* scalar,
-               uint8_t* final_state, cudaStream_t st) {
-    forest_fire_kernel<W><<<static_cast<unsigned>(n_items), 32 * W, 0, st>>>(
+mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, int n_steps,
+                      uint32_t t_dens, const RoundKeys& rk, const uint8_t* init, int32_t* counts,
+                      double* scalar, uint8_t* final_state, cudaStream_t st) {
+    const size_t smem = 2 * 2 * static_cast<size_t>(32 * W) * W * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(forest_fire_kernel<W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return cuda_status(e, "forest fire: shared memory attribute");
+    }
+    forest_fire_kernel<W><<<static_cast<unsigned>(n_items), ff_threads<W>(), smem, st>>>(
         dps, n_reps, n_steps, t_dens, rk, init, counts, scalar, final_state);
+    return MRIP_OK;
 }
 
 }  // namespace
@@ -222,12 +216,14 @@ extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_
     const RoundKeys rk = expand_key(seed);
     const uint32_t t_dens = threshold32(density);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mrip_status rc = MRIP_OK;
     switch (L) {
-        case 32: launch_ff<1>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 64: launch_ff<2>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 128: launch_ff<4>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 256: launch_ff<8>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 512: launch_ff<16>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 32: rc = launch_ff<1>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 64: rc = launch_ff<2>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 128: rc = launch_ff<4>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 256: rc = launch_ff<8>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 512: rc = launch_ff<16>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
     }
+    if (rc != MRIP_OK) return rc;
     return launch_status("mrip_forest_fire_simulate");
 }
