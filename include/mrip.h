@@ -274,6 +274,27 @@ mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t n_reps
                                int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk,
                                int64_t *d_tau, void *stream);
 
+/* Same walk, same arguments and outputs as mrip_walk_simulate, for callers
+ * that cannot allocate device memory: code running inside a framework or
+ * memory pool that owns every device allocation, or a latency-critical loop
+ * where cudaMalloc (which can synchronize the device and can fail) is not
+ * allowed.  The paper has no counterpart; it is a deployment variant.
+ * The call allocates nothing: its scratch (work-stealing ticket, step-cap
+ * flag, radius and design-point tables) is a fixed array of 8,448 bytes
+ * inside the library, present on every GPU that loads it until the process
+ * exits.  Limit: n_dp <= 1024 (larger values return MRIP_EINVAL).  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress) and
+ * should therefore come before any stream capture on that device.  Every
+ * call reuses the same array -- it resets the ticket and flag itself -- so
+ * two calls whose work overlaps on the GPU (different streams, or another
+ * thread) race and must not be issued concurrently.  The call waits for its
+ * table upload on `stream` before launching.  A replication that reaches
+ * max_steps is written as -1; mrip_check_device_flags does not see it. */
+mrip_status mrip_walk_simulate_noalloc(const double *radii, int32_t n_dp, int64_t n_reps,
+                                       uint64_t seed, int64_t max_steps, int mapping,
+                                       int32_t warps_per_cta, int32_t ctas_per_sm,
+                                       int32_t chunk, int64_t *d_tau, void *stream);
+
 /* Synchronous.  MRIP_ESTEPCAP if any walk launched since the last check hit
  * its step cap (and clears the flag), else MRIP_OK. */
 mrip_status mrip_check_device_flags(void);

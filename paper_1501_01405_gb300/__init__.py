@@ -116,6 +116,19 @@ def mrip_walk_simulate(radii, n_reps, seed, max_steps, mapping, tau, warps_per_c
                                     int(chunk), _dev(tau, t.int64, "tau"), _stream(stream)))
 
 
+def mrip_walk_simulate_noalloc(radii, n_reps, seed, max_steps, mapping, tau, warps_per_cta=0,
+                               ctas_per_sm=0, chunk=0, stream=None):
+    """mrip_walk_simulate for callers that cannot allocate device memory: its
+    scratch is a fixed array inside the library (at most 1024 radii); calls
+    must not overlap on the GPU."""
+    t = _t()
+    r, rp = _host(radii, np.float64)
+    _check(lib().mrip_walk_simulate_noalloc(rp, r.size, int(n_reps), int(seed), int(max_steps),
+                                            int(mapping), int(warps_per_cta), int(ctas_per_sm),
+                                            int(chunk), _dev(tau, t.int64, "tau"),
+                                            _stream(stream)))
+
+
 def mrip_check_device_flags():
     _check(lib().mrip_check_device_flags())
 

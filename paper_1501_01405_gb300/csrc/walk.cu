@@ -21,7 +21,9 @@
 //               16-move words, a warp scan of their displacements gives each
 //               lane's start, and a ballot finds the first exit.
 #include <algorithm>
+#include <mutex>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -309,9 +311,129 @@ mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>&
     return MRIP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Entry point for callers that cannot allocate device memory.
+//
+// Its scratch (work-stealing ticket, step-cap flag, radius and design-point
+// tables) lives in one file-scope device array instead of library-allocated
+// buffers.  Host code cannot pass the array's name to a kernel (in host code
+// it is only a stand-in); each device's address is looked up once with
+// cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxDp = 1024;
+constexpr size_t kNoAllocHeader = 256;  // [0, 8) ticket, [8, 12) step-cap flag
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * sizeof(int32_t) * kNoAllocMaxDp;
+
+static __device__ __align__(256) unsigned char g_walk_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[64] = {nullptr};
+
+mrip_status noalloc_scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(MRIP_EUNSUPPORTED, "mrip_walk_simulate_noalloc: device index >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_walk_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                               "mrip_walk_simulate_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return MRIP_OK;
+}
+}  // namespace
+
 }  // namespace mrip
 
 using namespace mrip;
+
+extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n_dp, int64_t n_reps,
+                                                  uint64_t seed, int64_t max_steps, int mapping,
+                                                  int32_t warps_per_cta, int32_t ctas_per_sm,
+                                                  int32_t chunk, int64_t* d_tau, void* stream) {
+    if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: negative size");
+    if (n_dp > kNoAllocMaxDp)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: n_dp " + std::to_string(n_dp) +
+                                     " exceeds its fixed scratch limit of " +
+                                     std::to_string(kNoAllocMaxDp) + " design points");
+    if (n_reps > 0xFFFFFFFFll) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: n_reps < 2^32");
+    if (max_steps < 1 || max_steps > (1LL << 38))
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: max_steps in 1..2^38");
+    if (chunk < 0 || chunk > (1 << 20))
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: chunk in 0..2^20");
+    if (static_cast<long long>(n_dp) * n_reps == 0) return MRIP_OK;
+    if (!radii || !d_tau) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: null pointer");
+    // processing order on the stack: largest radius first (stable insertion sort)
+    int32_t r_by_pos[kNoAllocMaxDp];
+    int32_t dp_by_pos[kNoAllocMaxDp];
+    for (int32_t i = 0; i < n_dp; ++i) {
+        const double r = radii[i];
+        if (!(r >= 1.0 && r <= 65536.0) || r != static_cast<double>(static_cast<int32_t>(r)))
+            return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: R must be an integer in 1..65536");
+        int32_t pos = i;
+        while (pos > 0 && r_by_pos[pos - 1] < static_cast<int32_t>(r)) {
+            r_by_pos[pos] = r_by_pos[pos - 1];
+            dp_by_pos[pos] = dp_by_pos[pos - 1];
+            --pos;
+        }
+        r_by_pos[pos] = static_cast<int32_t>(r);
+        dp_by_pos[pos] = i;
+    }
+    if (mapping != MRIP_MAP_AUTO && mapping != MRIP_MAP_PERSISTENT && mapping != MRIP_MAP_THREAD &&
+        mapping != MRIP_MAP_WARP_1LANE && mapping != MRIP_MAP_WARP_COOP)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: unknown mapping");
+    const int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
+    const int cps = ctas_per_sm > 0 ? ctas_per_sm : 4;
+    if (wpc > 32 || cps > 64)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: warps_per_cta <= 32, ctas_per_sm <= 64");
+
+    void* base_v = nullptr;
+    mrip_status s = noalloc_scratch_address(&base_v);
+    if (s != MRIP_OK) return s;
+    unsigned char* base = static_cast<unsigned char*>(base_v);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t tab = static_cast<size_t>(n_dp) * sizeof(int32_t);
+    int32_t* d_r = reinterpret_cast<int32_t*>(base + kNoAllocHeader);
+    int32_t* d_d = reinterpret_cast<int32_t*>(base + kNoAllocHeader + tab);
+    // the ticket and the flag must start at zero; the tables are overwritten
+    cudaError_t e = cudaMemsetAsync(base, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, r_by_pos, tab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_d, dp_by_pos, tab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables live on this stack frame
+    if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate_noalloc: scratch set-up");
+
+    WalkJob job;
+    job.radius = d_r;
+    job.dp_of = d_d;
+    job.n_reps = n_reps;
+    job.total = static_cast<long long>(n_dp) * n_reps;
+    job.max_steps = max_steps;
+    job.chunk = chunk > 0 ? chunk : 64;
+    job.tau = d_tau;
+    job.ticket = reinterpret_cast<unsigned long long*>(base);
+    job.err = reinterpret_cast<int*>(base + 8);
+    const RoundKeys rk = expand_key(seed);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms < 1) return cuda_status(e, "mrip_walk_simulate_noalloc: SM count");
+    if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_PERSISTENT) {
+        walk_persistent_kernel<<<sms * cps, 32 * wpc, 0, st>>>(job, rk);
+    } else if (mapping == MRIP_MAP_THREAD) {
+        walk_serial_kernel<false><<<ceil_div_u(job.total, 128), 128, 0, st>>>(job, rk);
+    } else if (mapping == MRIP_MAP_WARP_1LANE) {
+        walk_serial_kernel<true><<<ceil_div_u(job.total * 32, 128), 128, 0, st>>>(job, rk);
+    } else {
+        walk_warp_coop_kernel<<<ceil_div_u(job.total * 32, 128), 128, 0, st>>>(job, rk);
+    }
+    return launch_status("mrip_walk_simulate_noalloc");
+}
 
 extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int64_t n_reps,
                                           uint64_t seed, int64_t max_steps, int mapping,
