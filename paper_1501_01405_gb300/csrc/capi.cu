@@ -11,80 +11,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "model.cuh"
 
-namespace mrip {
-// defined in the model and statistics translation units
-mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_pos, int32_t n_dp,
-                        int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
-                        int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
-                        unsigned long long* d_ticket, cudaStream_t st);
-mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>& r_by_pos,
-                        std::vector<int32_t>& dp_by_pos);
-mrip_status stats_reduce_double(const double* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                                cudaStream_t st);
-mrip_status stats_reduce_int64(const int64_t* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                               cudaStream_t st);
-mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t n_reps,
-                        uint64_t seed, const mrip_cv_params* p, mrip_stat* plain_out,
-                        mrip_cv_stat* cv_out, float* loss_out);
-}  // namespace mrip
-
-struct Plan {
-    int mapping = MRIP_MAP_AUTO;
-    int warps_per_cta = 0;
-    int ctas_per_sm = 0;
-    int chunk = 0;
-};
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    bool ensure(size_t bytes) {
-        if (bytes <= cap && p) return true;
-        if (p) {
-            cudaFree(p);
-            p = nullptr;
-            cap = 0;
-        }
-        if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        cap = bytes < 256 ? 256 : bytes;
-        return true;
-    }
-    template <typename T>
-    T* as() const {
-        return static_cast<T*>(p);
-    }
-};
-
-struct mrip_model {
-    int kind = 0;
-    mrip_mm1_params mm1{};
-    mrip_tandem3_params tandem{};
-    mrip_forest_fire_params ff{};
-    mrip_walk_params walk{};
-    cudaStream_t stream = nullptr;
-    Plan plan;
-    DevBuf dps, out0, out1, nmm2, walk_tab, ticket;
-    std::vector<double> host_dps;
-    int32_t n_dp = 0;
-    int64_t n_reps = 0;
-    bool has_run = false;
-    // graph cache
-    cudaGraphExec_t exec = nullptr;
-    int32_t g_n_dp = -1;
-    int64_t g_n_reps = -1;
-    uint64_t g_seed = 0;
-    Plan g_plan;
-    ~mrip_model() {
-        if (exec) cudaGraphExecDestroy(exec);
-    }
-};
 
 namespace mrip {
 

@@ -38,27 +38,34 @@ inline RoundKeys expand_key(uint64_t seed) {
 // One Philox4x32 round: products of (0xD2511F53, x0) and (0xCD9E8D57, x2);
 // high halves xored with the other words and the round key; low halves
 // moved to positions 1 and 3.
-__device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_t& x2,
-                                             uint32_t& x3, uint32_t ka, uint32_t kb) {
+__host__ __device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_t& x2,
+                                                      uint32_t& x3, uint32_t ka, uint32_t kb) {
+#ifdef __CUDA_ARCH__
     const uint32_t p0_lo = 0xD2511F53u * x0;
     const uint32_t p0_hi = __umulhi(0xD2511F53u, x0);
     const uint32_t p1_lo = 0xCD9E8D57u * x2;
     const uint32_t p1_hi = __umulhi(0xCD9E8D57u, x2);
+#else
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * x0;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * x2;
+    const uint32_t p0_lo = static_cast<uint32_t>(p0), p0_hi = static_cast<uint32_t>(p0 >> 32);
+    const uint32_t p1_lo = static_cast<uint32_t>(p1), p1_hi = static_cast<uint32_t>(p1 >> 32);
+#endif
     x0 = p1_hi ^ x1 ^ ka;
     x1 = p1_lo;
     x2 = p0_hi ^ x3 ^ kb;
     x3 = p0_lo;
 }
 
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        const RoundKeys& rk) {
+__host__ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, const RoundKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, rk.k0[r], rk.k1[r]);
     return make_uint4(c0, c1, c2, c3);
 }
 
 // Counter word 3: stream tag in the top byte, design point below.
-__device__ __forceinline__ uint32_t stream_word(uint32_t tag, uint32_t dp) {
+__host__ __device__ __forceinline__ uint32_t stream_word(uint32_t tag, uint32_t dp) {
     return (tag << 24) | dp;
 }
 

@@ -21,6 +21,7 @@
 // shared-memory atomic; counts are flushed to global memory every 64 steps
 // (coalesced) from a double-buffered slot array.
 #include "common.cuh"
+#include "model.cuh"
 
 namespace mrip {
 namespace {
@@ -35,7 +36,7 @@ constexpr int ff_threads() {
 
 template <int W>
 __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
-    const double* __restrict__ dps, long long n_reps, int n_steps, uint32_t t_dens,
+    const double* __restrict__ dps, long long n_reps, long long rep0, int n_steps, uint32_t t_dens,
     const __grid_constant__ RoundKeys rk, const uint8_t* __restrict__ init,
     int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
     constexpr int L = 32 * W;
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
     const int warp = threadIdx.x >> 5;
     const long long item = blockIdx.x;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
-    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const uint32_t t_grow = threshold32(dps[2 * dp]);
     const uint32_t t_light = threshold32(dps[2 * dp + 1]);
     const uint32_t c3 = stream_word(0u, dp);
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
 }
 
 template <int W>
-mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, int n_steps,
+mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, long long rep0, int n_steps,
                       uint32_t t_dens, const RoundKeys& rk, const uint8_t* init, int32_t* counts,
                       double* scalar, uint8_t* final_state, cudaStream_t st) {
     const size_t smem = 2 * 2 * static_cast<size_t>(32 * W) * W * sizeof(uint32_t);
@@ -184,7 +185,7 @@ mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, in
         if (e != cudaSuccess) return cuda_status(e, "forest fire: shared memory attribute");
     }
     forest_fire_kernel<W><<<static_cast<unsigned>(n_items), ff_threads<W>(), smem, st>>>(
-        dps, n_reps, n_steps, t_dens, rk, init, counts, scalar, final_state);
+        dps, n_reps, rep0, n_steps, t_dens, rk, init, counts, scalar, final_state);
     return MRIP_OK;
 }
 
@@ -193,19 +194,18 @@ mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, in
 
 using namespace mrip;
 
-extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
-                                                 int32_t L, int32_t n_steps, double density,
-                                                 uint64_t seed, const uint8_t* d_init,
-                                                 int32_t* d_counts, double* d_scalar,
-                                                 uint8_t* d_final, void* stream) {
-    if (n_dp < 0 || n_reps < 0 || n_steps < 0)
+namespace mrip {
+mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps, int32_t L,
+                               int32_t n_steps, double density, uint64_t seed, const uint8_t* d_init,
+                               int32_t* d_counts, double* d_scalar, uint8_t* d_final, cudaStream_t st) {
+    if (n_dp < 0 || n_reps < 0 || n_steps < 0 || rep0 < 0)
         return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: negative size");
     if (L < 32 || L > 512 || L % 32 != 0 || (L & (L - 1)) != 0)
         return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: L must be 32, 64, 128, 256 or 512");
     if (!(density >= 0.0 && density < 1.0))
         return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: density must be in [0, 1)");
-    if (n_dp >= (1 << 24) || n_reps > 0xFFFFFFFFll)
-        return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: n_dp < 2^24 and n_reps < 2^32");
+    if (n_dp >= (1 << 24) || rep0 + n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: n_dp < 2^24 and replication indices < 2^32");
     const long long n_items = static_cast<long long>(n_dp) * n_reps;
     if (n_items == 0) return MRIP_OK;
     if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: too many replications");
@@ -215,15 +215,24 @@ extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_
         return fail(MRIP_EINVAL, "mrip_forest_fire_simulate: state buffers need 16-byte alignment");
     const RoundKeys rk = expand_key(seed);
     const uint32_t t_dens = threshold32(density);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     mrip_status rc = MRIP_OK;
     switch (L) {
-        case 32: rc = launch_ff<1>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 64: rc = launch_ff<2>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 128: rc = launch_ff<4>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 256: rc = launch_ff<8>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
-        case 512: rc = launch_ff<16>(d_dps, n_items, n_reps, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 32: rc = launch_ff<1>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 64: rc = launch_ff<2>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 128: rc = launch_ff<4>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 256: rc = launch_ff<8>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
+        case 512: rc = launch_ff<16>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, d_init, d_counts, d_scalar, d_final, st); break;
     }
     if (rc != MRIP_OK) return rc;
     return launch_status("mrip_forest_fire_simulate");
+}
+}  // namespace mrip
+
+extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+                                                 int32_t L, int32_t n_steps, double density,
+                                                 uint64_t seed, const uint8_t* d_init,
+                                                 int32_t* d_counts, double* d_scalar,
+                                                 uint8_t* d_final, void* stream) {
+    return forest_fire_launch(d_dps, n_dp, 0, n_reps, L, n_steps, density, seed, d_init, d_counts,
+                              d_scalar, d_final, static_cast<cudaStream_t>(stream));
 }

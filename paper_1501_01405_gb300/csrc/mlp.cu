@@ -1,33 +1,510 @@
-// Learned control variate: network stages (placeholder until the kernels land).
+// Learned control variate, network stages: a d_in -> 64 -> 64 -> 1 ReLU
+// network (d_in = 8 for the tandem queue, 6 for the forest fire) trained on
+// replications the engine generates, used as a control variate.  The paper
+// has no learned component; its estimator (the replication mean, Section 1)
+// stays the fallback and the judge.
+//
+// Arithmetic: parameters are FP32 masters; every matmul takes BF16 operands
+// (round to nearest even from FP32) and accumulates in FP32:
+//   forward  z1 = x~ W1~^T + b1, h1 = relu(z1); z2 = h1~ W2~^T + b2, h2 = relu(z2);
+//            yhat = h2~ . W3~ + b3
+//   backward dyhat = 2 (yhat - y) / B; dW3 = sum dyhat h2~; dz2 = dyhat W3~ [z2 > 0];
+//            dW2 = dz2~^T h1~; dz1 = (dz2~ W2~) [z1 > 0]; dW1 = dz1~^T x~;
+//            bias gradients are FP32 sums of the unrounded dz.
+// The matrices are 64 wide, so the passes are latency- not throughput-bound:
+// a CTA takes a tile of 32 samples with the BF16-rounded weights staged in
+// shared memory (both orientations of W2, so every inner product reads
+// consecutive words), and writes its per-parameter partial sums; a second
+// kernel adds the partials of all CTAs in a fixed order (deterministic) and,
+// during training, applies Adam in the same pass.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
 #include "common.cuh"
+#include "model.cuh"
 
 namespace mrip {
-mrip_status run_cv_impl(mrip_model*, const double*, int32_t, int64_t, uint64_t, const mrip_cv_params*,
-                        mrip_stat*, mrip_cv_stat*, float*) {
-    return fail(MRIP_EUNSUPPORTED, "control variate: not built yet");
+
+namespace {
+
+constexpr int H = 64;
+constexpr int kTile = 32;        // samples per CTA
+constexpr int kGradThreads = 256;
+constexpr int kMaxIn = 8;
+
+__host__ __device__ constexpr long long off_b1(int d) { return static_cast<long long>(H) * d; }
+__host__ __device__ constexpr long long off_w2(int d) { return off_b1(d) + H; }
+__host__ __device__ constexpr long long off_b2(int d) { return off_w2(d) + H * H; }
+__host__ __device__ constexpr long long off_w3(int d) { return off_b2(d) + H; }
+__host__ __device__ constexpr long long off_b3(int d) { return off_w3(d) + H; }
+__host__ __device__ constexpr long long n_params(int d) { return off_b3(d) + 1; }
+
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// He-uniform weights from stream tag 3: element e of (W1, W2, W3) reads words
+// 2(e mod 2), 2(e mod 2)+1 of block (c0 = e div 2, c1 = 0, rep 0, dp 0).
+__global__ void mlp_init_kernel(int d_in, const __grid_constant__ RoundKeys rk, float* theta) {
+    const long long n_w = static_cast<long long>(H) * d_in + H * H + H;
+    const long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (e < n_w) {
+        const uint4 b = philox(static_cast<uint32_t>(e >> 1), 0u, 0u, stream_word(3u, 0u), rk);
+        const double u = (e & 1) ? u53(b.z, b.w) : u53(b.x, b.y);
+        long long dst;
+        double fan;
+        if (e < static_cast<long long>(H) * d_in) {
+            dst = e;
+            fan = d_in;
+        } else if (e < static_cast<long long>(H) * d_in + H * H) {
+            dst = off_w2(d_in) + (e - static_cast<long long>(H) * d_in);
+            fan = H;
+        } else {
+            dst = off_w3(d_in) + (e - static_cast<long long>(H) * d_in - H * H);
+            fan = H;
+        }
+        theta[dst] = static_cast<float>((2.0 * u - 1.0) * sqrt(6.0 / fan));
+    }
+    // biases
+    if (e < H) {
+        theta[off_b1(d_in) + e] = 0.0f;
+        theta[off_b2(d_in) + e] = 0.0f;
+    }
+    if (e == 0) theta[off_b3(d_in)] = 0.0f;
 }
+
+// Which sample sits at batch position i.
+struct SampleMap {
+    const int64_t* idx;   // explicit indices, or null
+    unsigned long long a, b, n;  // affine permutation (a i + b) mod n when n > 0
+    long long off;        // batch offset within the epoch
+};
+
+__device__ __forceinline__ long long sample_of(const SampleMap& m, long long i) {
+    if (m.idx) return m.idx[i];
+    const unsigned long long k = static_cast<unsigned long long>(m.off + i);
+    if (m.n > 0) return static_cast<long long>((m.a * k + m.b) % m.n);
+    return static_cast<long long>(k);
+}
+
+struct GradSmem {
+    float w1t[kMaxIn][H];  // [k][u]
+    float w2t[H][H];       // [u][v]
+    float w2[H][H];        // [v][u]
+    float w3[H], b1[H], b2[H];
+    float b3;
+    float xt[kTile][kMaxIn];
+    float h1[kTile][H];
+    float h1t[kTile][H];
+    float h2[kTile][H];
+    float h2t[kTile][H];
+    float dz2[kTile][H];
+    float dz2t[kTile][H];
+    float dz1[kTile][H];
+    float dy[kTile];
+    float ys[kTile];
+};
+
+// Forward + backward of one tile of kTile samples; partial[blockIdx][p] gets
+// the tile's gradient, partial_loss[blockIdx] its sum of squared residuals.
+__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
+    const float* __restrict__ theta, int d_in, const float* __restrict__ X, long long n_total,
+    const float* __restrict__ Y, SampleMap map, long long B, float* __restrict__ partial,
+    float* __restrict__ partial_loss) {
+    extern __shared__ unsigned char smem_raw[];
+    GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+    const int t = threadIdx.x;
+    const long long P = n_params(d_in);
+
+    for (int i = t; i < H * d_in; i += kGradThreads) {
+        const int u = i / d_in, k = i - u * d_in;
+        S.w1t[k][u] = bf(theta[i]);
+    }
+    for (int i = t; i < H * H; i += kGradThreads) {
+        const int v = i / H, u = i - v * H;
+        const float w = bf(theta[off_w2(d_in) + i]);
+        S.w2[v][u] = w;
+        S.w2t[u][v] = w;
+    }
+    for (int i = t; i < H; i += kGradThreads) {
+        S.w3[i] = bf(theta[off_w3(d_in) + i]);
+        S.b1[i] = theta[off_b1(d_in) + i];
+        S.b2[i] = theta[off_b2(d_in) + i];
+    }
+    if (t == 0) S.b3 = theta[off_b3(d_in)];
+    const long long base = static_cast<long long>(blockIdx.x) * kTile;
+    for (int i = t; i < kTile * kMaxIn; i += kGradThreads) {
+        const int s = i / kMaxIn, k = i - s * kMaxIn;
+        float v = 0.0f;
+        if (base + s < B && k < d_in) v = bf(X[k * n_total + sample_of(map, base + s)]);
+        S.xt[s][k] = v;
+    }
+    if (t < kTile) S.ys[t] = (base + t < B) ? Y[sample_of(map, base + t)] : 0.0f;
+    __syncthreads();
+
+    const int s = t >> 3;  // sample of this thread for the per-sample passes
+    const int g = t & 7;   // its slice of units: g, g + 8, ..., g + 56
+    // layer 1
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int u = g + 8 * i;
+        float acc = 0.0f;
+        for (int k = 0; k < d_in; ++k) acc = fmaf(S.xt[s][k], S.w1t[k][u], acc);
+        const float h = fmaxf(acc + S.b1[u], 0.0f);
+        S.h1[s][u] = h;
+        S.h1t[s][u] = bf(h);
+    }
+    __syncthreads();
+    // layer 2
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int v = g + 8 * i;
+        float acc = 0.0f;
+#pragma unroll 8
+        for (int u = 0; u < H; ++u) acc = fmaf(S.h1t[s][u], S.w2t[u][v], acc);
+        const float h = fmaxf(acc + S.b2[v], 0.0f);
+        S.h2[s][v] = h;
+        S.h2t[s][v] = bf(h);
+    }
+    __syncthreads();
+    // output and residual (8 threads per sample, lanes 8s'..8s'+7 of a warp)
+    {
+        float part = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) part = fmaf(S.h2t[s][g + 8 * i], S.w3[g + 8 * i], part);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 4);
+        if (g == 0) {
+            const bool valid = base + s < B;
+            const float r = valid ? (part + S.b3) - S.ys[s] : 0.0f;
+            S.dy[s] = valid ? 2.0f * r / static_cast<float>(B) : 0.0f;
+            S.ys[s] = r * r;  // reuse: squared residual
+        }
+    }
+    __syncthreads();
+    // dz2 = dyhat W3~ [z2 > 0]
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int v = g + 8 * i;
+        const float d = S.h2[s][v] > 0.0f ? S.dy[s] * S.w3[v] : 0.0f;
+        S.dz2[s][v] = d;
+        S.dz2t[s][v] = bf(d);
+    }
+    __syncthreads();
+    // dz1 = (dz2~ W2~) [z1 > 0]
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int u = g + 8 * i;
+        float acc = 0.0f;
+#pragma unroll 8
+        for (int v = 0; v < H; ++v) acc = fmaf(S.dz2t[s][v], S.w2[v][u], acc);
+        S.dz1[s][u] = S.h1[s][u] > 0.0f ? acc : 0.0f;
+    }
+    __syncthreads();
+
+    // weight gradients of the tile
+    float* out = partial + static_cast<long long>(blockIdx.x) * P;
+    {
+        const int v = t >> 2;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int u = (t & 3) + 4 * j;
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int q = 0; q < kTile; ++q) acc = fmaf(S.dz2t[q][v], S.h1t[q][u], acc);
+            out[off_w2(d_in) + v * H + u] = acc;
+        }
+    }
+    for (int i = t; i < H * d_in; i += kGradThreads) {
+        const int u = i / d_in, k = i - u * d_in;
+        float acc = 0.0f;
+        for (int q = 0; q < kTile; ++q) acc = fmaf(bf(S.dz1[q][u]), S.xt[q][k], acc);
+        out[i] = acc;
+    }
+    if (t < H) {
+        float a3 = 0.0f, a2 = 0.0f, a1 = 0.0f;
+        for (int q = 0; q < kTile; ++q) {
+            a3 = fmaf(S.dy[q], S.h2t[q][t], a3);
+            a2 += S.dz2[q][t];
+            a1 += S.dz1[q][t];
+        }
+        out[off_w3(d_in) + t] = a3;
+        out[off_b2(d_in) + t] = a2;
+        out[off_b1(d_in) + t] = a1;
+    }
+    if (t == H) {
+        float a = 0.0f, l = 0.0f;
+        for (int q = 0; q < kTile; ++q) {
+            a += S.dy[q];
+            l += S.ys[q];
+        }
+        out[off_b3(d_in)] = a;
+        partial_loss[blockIdx.x] = l;
+    }
+}
+
+// grad[p] = sum over CTAs of partial[c][p] (fixed order); optionally Adam.
+template <bool kAdam>
+__global__ void mlp_reduce_kernel(const float* __restrict__ partial, const float* __restrict__ partial_loss,
+                                  int n_cta, long long P, long long B, float* __restrict__ grad,
+                                  float* __restrict__ loss, float* __restrict__ theta, float* __restrict__ m,
+                                  float* __restrict__ v, float lr, float beta1, float beta2, float eps,
+                                  float bc1, float bc2) {
+    const long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (p < P) {
+        float acc = 0.0f;
+        for (int c = 0; c < n_cta; ++c) acc += partial[static_cast<long long>(c) * P + p];
+        if (grad) grad[p] = acc;
+        if (kAdam) {
+            const float mi = beta1 * m[p] + (1.0f - beta1) * acc;
+            const float vi = beta2 * v[p] + (1.0f - beta2) * acc * acc;
+            m[p] = mi;
+            v[p] = vi;
+            const float mhat = mi / bc1;
+            const float vhat = vi / bc2;
+            theta[p] = theta[p] - lr * mhat / (sqrtf(vhat) + eps);
+        }
+    }
+    if (p == 0 && loss) {
+        float l = 0.0f;
+        for (int c = 0; c < n_cta; ++c) l += partial_loss[c];
+        *loss = l / static_cast<float>(B);
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float beta1, float beta2,
+                            float eps, float bc1, float bc2) {
+    const long long p = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (p >= n) return;
+    const float gi = g[p];
+    const float mi = beta1 * m[p] + (1.0f - beta1) * gi;
+    const float vi = beta2 * v[p] + (1.0f - beta2) * gi * gi;
+    m[p] = mi;
+    v[p] = vi;
+    theta[p] = theta[p] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// Inference, one sample per thread, weights (BF16-rounded) in shared memory.
+__global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ theta, int d_in,
+                                                         const float* __restrict__ X, long long n,
+                                                         float* __restrict__ yhat) {
+    __shared__ float w1[H][kMaxIn];
+    __shared__ __align__(16) float w2[H][H];  // [v][u]
+    __shared__ float w3[H], b1[H], b2[H];
+    __shared__ float b3;
+    for (int i = threadIdx.x; i < H * kMaxIn; i += blockDim.x) {
+        const int u = i / kMaxIn, k = i - u * kMaxIn;
+        w1[u][k] = k < d_in ? bf(theta[u * d_in + k]) : 0.0f;
+    }
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) w2[i / H][i % H] = bf(theta[off_w2(d_in) + i]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        w3[i] = bf(theta[off_w3(d_in) + i]);
+        b1[i] = theta[off_b1(d_in) + i];
+        b2[i] = theta[off_b2(d_in) + i];
+    }
+    if (threadIdx.x == 0) b3 = theta[off_b3(d_in)];
+    __syncthreads();
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    float x[kMaxIn];
+#pragma unroll
+    for (int k = 0; k < kMaxIn; ++k) x[k] = k < d_in ? bf(X[k * n + i]) : 0.0f;
+    float h1[H];
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kMaxIn; ++k) acc = fmaf(x[k], w1[u][k], acc);
+        h1[u] = bf(fmaxf(acc + b1[u], 0.0f));
+    }
+    float out = 0.0f;
+    for (int v = 0; v < H; ++v) {
+        float acc = 0.0f;
+        const float4* row = reinterpret_cast<const float4*>(&w2[v][0]);
+#pragma unroll
+        for (int q = 0; q < H / 4; ++q) {
+            const float4 w = row[q];
+            acc = fmaf(h1[4 * q], w.x, acc);
+            acc = fmaf(h1[4 * q + 1], w.y, acc);
+            acc = fmaf(h1[4 * q + 2], w.z, acc);
+            acc = fmaf(h1[4 * q + 3], w.w, acc);
+        }
+        out = fmaf(bf(fmaxf(acc + b2[v], 0.0f)), w3[v], out);
+    }
+    yhat[i] = out + b3;
+}
+
+// Control-variate reduction of one design point per CTA (FP64, two passes,
+// fixed-order tree sums).
+constexpr int kCvThreads = 256;
+
+__device__ double block_sum(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int stride = kCvThreads / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) sh[threadIdx.x] += sh[threadIdx.x + stride];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kCvThreads) cv_reduce_kernel(const double* __restrict__ y,
+                                                               const double* __restrict__ g, long long n,
+                                                               const double* __restrict__ gc, long long m,
+                                                               double* __restrict__ out) {
+    __shared__ double sh[kCvThreads];
+    const long long dp = blockIdx.x;
+    const double* yr = y + dp * n;
+    const double* gr = g + dp * n;
+    const double* cr = gc + dp * m;
+    double sy = 0.0, sg = 0.0, sc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += kCvThreads) {
+        sy += yr[i];
+        sg += gr[i];
+    }
+    for (long long i = threadIdx.x; i < m; i += kCvThreads) sc += cr[i];
+    const double ybar = block_sum(sy, sh) / static_cast<double>(n);
+    const double gbar = block_sum(sg, sh) / static_cast<double>(n);
+    const double cbar = block_sum(sc, sh) / static_cast<double>(m);
+    double sxy = 0.0, sgg = 0.0, scc = 0.0;
+    for (long long i = threadIdx.x; i < n; i += kCvThreads) {
+        const double dy = yr[i] - ybar, dg = gr[i] - gbar;
+        sxy += dy * dg;
+        sgg += dg * dg;
+    }
+    for (long long i = threadIdx.x; i < m; i += kCvThreads) {
+        const double dc = cr[i] - cbar;
+        scc += dc * dc;
+    }
+    const double cov = block_sum(sxy, sh) / static_cast<double>(n - 1);
+    const double var_g = block_sum(sgg, sh) / static_cast<double>(n - 1);
+    const double var_c = block_sum(scc, sh) / static_cast<double>(m - 1);
+    const double beta = var_g > 0.0 ? cov / var_g : 0.0;
+    double sr = 0.0;
+    for (long long i = threadIdx.x; i < n; i += kCvThreads) sr += yr[i] - beta * gr[i];
+    const double rbar = block_sum(sr, sh) / static_cast<double>(n);
+    double srr = 0.0;
+    for (long long i = threadIdx.x; i < n; i += kCvThreads) {
+        const double d = (yr[i] - beta * gr[i]) - rbar;
+        srr += d * d;
+    }
+    const double s_r2 = block_sum(srr, sh) / static_cast<double>(n - 2);
+    if (threadIdx.x == 0) {
+        out[5 * dp] = beta;
+        out[5 * dp + 1] = ybar - beta * (gbar - cbar);
+        out[5 * dp + 2] = s_r2 / static_cast<double>(n) + beta * beta * var_c / static_cast<double>(m);
+        out[5 * dp + 3] = ybar;
+        out[5 * dp + 4] = gbar - cbar;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// internal launchers used by the control-variate driver
+// ---------------------------------------------------------------------------
+long long mlp_params(int d_in) { return n_params(d_in); }
+
+mrip_status mlp_init(int d_in, uint64_t seed, float* theta, cudaStream_t st) {
+    const long long n_w = static_cast<long long>(H) * d_in + H * H + H;
+    mlp_init_kernel<<<ceil_div_u(n_w, 256), 256, 0, st>>>(d_in, expand_key(seed), theta);
+    return launch_status("mlp init");
+}
+
+size_t mlp_grad_partial_floats(int d_in, long long B) {
+    return static_cast<size_t>((B + kTile - 1) / kTile) * static_cast<size_t>(n_params(d_in) + 1);
+}
+
+// One gradient (and optionally Adam) step over batch positions [0, B) of map.
+mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long n_total, const float* Y,
+                     const int64_t* idx, unsigned long long a, unsigned long long b, unsigned long long n_perm,
+                     long long off, long long B, float* partial, float* grad, float* loss, float* theta,
+                     float* m, float* v, const float* adam /* lr, b1, b2, eps, bc1, bc2 */, cudaStream_t st) {
+    const int n_cta = static_cast<int>((B + kTile - 1) / kTile);
+    const long long P = n_params(d_in);
+    float* part_loss = partial + static_cast<long long>(n_cta) * P;
+    SampleMap map{idx, a, b, n_perm, off};
+    cudaError_t e = cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sizeof(GradSmem)));
+    if (e != cudaSuccess) return cuda_status(e, "mlp: shared memory attribute");
+    mlp_grad_kernel<<<n_cta, kGradThreads, sizeof(GradSmem), st>>>(theta_in, d_in, X, n_total, Y, map, B,
+                                                                   partial, part_loss);
+    mrip_status s = launch_status("mlp grad");
+    if (s != MRIP_OK) return s;
+    if (adam) {
+        mlp_reduce_kernel<true><<<ceil_div_u(P, 256), 256, 0, st>>>(
+            partial, part_loss, n_cta, P, B, grad, loss, theta, m, v, adam[0], adam[1], adam[2], adam[3],
+            adam[4], adam[5]);
+    } else {
+        mlp_reduce_kernel<false><<<ceil_div_u(P, 256), 256, 0, st>>>(
+            partial, part_loss, n_cta, P, B, grad, loss, nullptr, nullptr, nullptr, 0, 0, 0, 0, 1, 1);
+    }
+    return launch_status("mlp reduce");
+}
+
+mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat, cudaStream_t st) {
+    if (n == 0) return MRIP_OK;
+    mlp_forward_kernel<<<ceil_div_u(n, 128), 128, 0, st>>>(theta, d_in, X, n, yhat);
+    return launch_status("mlp forward");
+}
+
+mrip_status cv_reduce(const double* y, const double* g, long long n, const double* gc, long long m, int n_dp,
+                      double* out, cudaStream_t st) {
+    if (n_dp == 0) return MRIP_OK;
+    cv_reduce_kernel<<<n_dp, kCvThreads, 0, st>>>(y, g, n, gc, m, out);
+    return launch_status("cv reduce");
+}
+
 }  // namespace mrip
 
 using namespace mrip;
 
-extern "C" int64_t mrip_mlp_param_count(int32_t d_in) {
-    return 64LL * d_in + 64 + 64 * 64 + 64 + 64 + 1;
+extern "C" int64_t mrip_mlp_param_count(int32_t d_in) { return d_in >= 1 && d_in <= 8 ? n_params(d_in) : -1; }
+
+extern "C" mrip_status mrip_mlp_init(int32_t d_in, uint64_t seed, float* d_theta, void* stream) {
+    if (d_in < 1 || d_in > kMaxIn) return fail(MRIP_EINVAL, "mrip_mlp_init: d_in in 1..8");
+    if (!d_theta) return fail(MRIP_EINVAL, "mrip_mlp_init: null theta");
+    return mlp_init(d_in, seed, d_theta, static_cast<cudaStream_t>(stream));
 }
-extern "C" mrip_status mrip_mlp_init(int32_t, uint64_t, float*, void*) {
-    return fail(MRIP_EUNSUPPORTED, "mlp: not built yet");
+
+extern "C" mrip_status mrip_mlp_forward(const float* d_theta, int32_t d_in, const float* d_x, int64_t n,
+                                        float* d_yhat, void* stream) {
+    if (d_in < 1 || d_in > kMaxIn || n < 0) return fail(MRIP_EINVAL, "mrip_mlp_forward: d_in in 1..8, n >= 0");
+    if (n > 0 && (!d_theta || !d_x || !d_yhat)) return fail(MRIP_EINVAL, "mrip_mlp_forward: null pointer");
+    return mlp_forward(d_theta, d_in, d_x, n, d_yhat, static_cast<cudaStream_t>(stream));
 }
-extern "C" mrip_status mrip_mlp_forward(const float*, int32_t, const float*, int64_t, float*, void*) {
-    return fail(MRIP_EUNSUPPORTED, "mlp: not built yet");
+
+extern "C" mrip_status mrip_mlp_loss_grad(const float* d_theta, int32_t d_in, const float* d_x, const float* d_y,
+                                          int64_t n, const int64_t* d_idx, int64_t B, float* d_grad,
+                                          float* d_loss, void* stream) {
+    if (d_in < 1 || d_in > kMaxIn || n < 1 || B < 1 || (!d_idx && B > n))
+        return fail(MRIP_EINVAL, "mrip_mlp_loss_grad: d_in in 1..8, 1 <= B (<= n without idx)");
+    if (!d_theta || !d_x || !d_y || !d_grad) return fail(MRIP_EINVAL, "mrip_mlp_loss_grad: null pointer");
+    const size_t need = mlp_grad_partial_floats(d_in, B) * sizeof(float);
+    float* partial = static_cast<float*>(scratch(need, 2));
+    if (!partial) return fail(MRIP_ENOMEM, "mrip_mlp_loss_grad: scratch allocation failed");
+    return mlp_step(d_theta, d_in, d_x, n, d_y, d_idx, 0, 0, 0, 0, B, partial, d_grad, d_loss, nullptr,
+                    nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
-extern "C" mrip_status mrip_mlp_loss_grad(const float*, int32_t, const float*, const float*, int64_t,
-                                          const int64_t*, int64_t, float*, float*, void*) {
-    return fail(MRIP_EUNSUPPORTED, "mlp: not built yet");
+
+extern "C" mrip_status mrip_adam_step(float* d_theta, float* d_m, float* d_v, const float* d_grad, int64_t n,
+                                      int64_t t, float lr, float beta1, float beta2, float eps, void* stream) {
+    if (n < 0 || t < 1) return fail(MRIP_EINVAL, "mrip_adam_step: n >= 0, t >= 1");
+    if (n == 0) return MRIP_OK;
+    if (!d_theta || !d_m || !d_v || !d_grad) return fail(MRIP_EINVAL, "mrip_adam_step: null pointer");
+    const float bc1 = static_cast<float>(1.0 - std::pow(static_cast<double>(beta1), static_cast<double>(t)));
+    const float bc2 = static_cast<float>(1.0 - std::pow(static_cast<double>(beta2), static_cast<double>(t)));
+    adam_kernel<<<ceil_div_u(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_theta, d_m, d_v, d_grad, n,
+                                                                                  lr, beta1, beta2, eps, bc1, bc2);
+    return launch_status("mrip_adam_step");
 }
-extern "C" mrip_status mrip_adam_step(float*, float*, float*, const float*, int64_t, int64_t, float, float,
-                                      float, float, void*) {
-    return fail(MRIP_EUNSUPPORTED, "mlp: not built yet");
-}
-extern "C" mrip_status mrip_cv_reduce(const double*, const double*, int64_t, const double*, int64_t, int32_t,
-                                      double*, void*) {
-    return fail(MRIP_EUNSUPPORTED, "cv: not built yet");
+
+extern "C" mrip_status mrip_cv_reduce(const double* d_y, const double* d_g, int64_t n, const double* d_gc,
+                                      int64_t m, int32_t n_dp, double* d_out, void* stream) {
+    if (n < 3 || m < 2 || n_dp < 0) return fail(MRIP_EINVAL, "mrip_cv_reduce: n >= 3, m >= 2, n_dp >= 0");
+    if (n_dp > 0 && (!d_y || !d_g || !d_gc || !d_out)) return fail(MRIP_EINVAL, "mrip_cv_reduce: null pointer");
+    return cv_reduce(d_y, d_g, n, d_gc, m, n_dp, d_out, static_cast<cudaStream_t>(stream));
 }

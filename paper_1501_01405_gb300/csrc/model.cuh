@@ -1,0 +1,102 @@
+// Private declarations shared by the engine's translation units: the model
+// handle, its device buffers and the internal launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/mrip.h"
+
+struct Plan {
+    int mapping = MRIP_MAP_AUTO;
+    int warps_per_cta = 0;
+    int ctas_per_sm = 0;
+    int chunk = 0;
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    bool ensure(size_t bytes) {
+        if (bytes <= cap && p) return true;
+        if (p) {
+            cudaFree(p);
+            p = nullptr;
+            cap = 0;
+        }
+        if (cudaMalloc(&p, bytes < 256 ? 256 : bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cap = bytes < 256 ? 256 : bytes;
+        return true;
+    }
+    template <typename T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+struct mrip_model {
+    int kind = 0;
+    mrip_mm1_params mm1{};
+    mrip_tandem3_params tandem{};
+    mrip_forest_fire_params ff{};
+    mrip_walk_params walk{};
+    cudaStream_t stream = nullptr;
+    Plan plan;
+    DevBuf dps, out0, out1, nmm2, walk_tab, ticket;
+    std::vector<double> host_dps;
+    int32_t n_dp = 0;
+    int64_t n_reps = 0;
+    bool has_run = false;
+    // graph cache
+    cudaGraphExec_t exec = nullptr;
+    int32_t g_n_dp = -1;
+    int64_t g_n_reps = -1;
+    uint64_t g_seed = 0;
+    Plan g_plan;
+    ~mrip_model() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+namespace mrip {
+int dp_dim(int kind);
+mrip_status check_dps(int kind, const double* dps, int32_t n_dp);
+mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_pos, int32_t n_dp,
+                        int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
+                        int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
+                        unsigned long long* d_ticket, cudaStream_t st);
+mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>& r_by_pos,
+                        std::vector<int32_t>& dp_by_pos);
+mrip_status stats_reduce_double(const double* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
+                                cudaStream_t st);
+mrip_status stats_reduce_int64(const int64_t* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
+                               cudaStream_t st);
+double t_critical(double conf, long long df);
+mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
+                               int32_t L, int32_t n_steps, double density, uint64_t seed,
+                               const uint8_t* d_init, int32_t* d_counts, double* d_scalar,
+                               uint8_t* d_final, cudaStream_t st);
+mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t n_reps,
+                        uint64_t seed, const mrip_cv_params* p, mrip_stat* plain_out,
+                        mrip_cv_stat* cv_out, float* loss_out);
+// network stages (mlp.cu)
+long long mlp_params(int d_in);
+mrip_status mlp_init(int d_in, uint64_t seed, float* theta, cudaStream_t st);
+size_t mlp_grad_partial_floats(int d_in, long long B);
+mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long n_total, const float* Y,
+                     const int64_t* idx, unsigned long long a, unsigned long long b, unsigned long long n_perm,
+                     long long off, long long B, float* partial, float* grad, float* loss, float* theta,
+                     float* m, float* v, const float* adam, cudaStream_t st);
+mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat,
+                        cudaStream_t st);
+mrip_status cv_reduce(const double* y, const double* g, long long n, const double* gc, long long m,
+                      int n_dp, double* out, cudaStream_t st);
+}  // namespace mrip
