@@ -158,8 +158,11 @@ mrip_status run_common(mrip_model* m, int32_t n_dp, int64_t n_reps, uint64_t see
             cudaGraphExecDestroy(m->exec);
             m->exec = nullptr;
         }
-        // the stage launchers touch lazily created scratch; create it before capture
+        // the stage launchers touch lazily created tables; create them before capture
         sm_count();
+        LogTable tab;
+        mrip_status ts = log_table(&tab);
+        if (ts != MRIP_OK) return ts;
         cudaStream_t cap = m->stream;
         bool own = false;
         if (cap == nullptr) {  // the legacy stream cannot be captured

@@ -75,9 +75,72 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
     return __ull2double_rn(bits >> 11) * 0x1p-53;
 }
 
-// Exponential variate by inversion, -log(1 - u) / rate, IEEE divide.
-__device__ __forceinline__ double expo_div(double u, double rate) {
-    return -log(1.0 - u) / rate;
+// ---------------------------------------------------------------------------
+// Exponential variates without the FP64 log.
+//
+// GB300's FP64 pipe retires about 2 FMAs per SM per clock, its integer pipes
+// over 40 multiplies, so -log(1 - u) is evaluated in 64-bit fixed point
+// (Tang's table-driven reduction, ACM TOMS 16(4), 1990, carried out in
+// integers).  With 1 - u = K 2^-53, K in [1, 2^53], K = 2^e M, M in [1, 2):
+//   -log(1 - u) = (53 - e) ln 2 - ln M,
+//   ln M = ln c_j + log1p(r),  r = M / c_j - 1,  |r| < 2^-9,
+// c_j the centre of the j-th of 256 slices of [1, 2) (j = the 8 bits after
+// the leading one), 1/c_j stored as a 63-bit fraction, ln c_j as a 64-bit
+// fraction, and log1p(r) = r + r^2 (-1/2 + r/3 - r^2/4 + r^3/5 - r^4/6)
+// (truncation below 2^-64), r in signed Q.64 and the bracket in Q.63.  The result carries an absolute
+// error below 2^-56 before its one rounding to double, i.e. within about an
+// ulp for -log(1 - u) > 1/16 and far below the ulp of any sum it enters.
+// ---------------------------------------------------------------------------
+struct __align__(16) LogSlice {
+    unsigned long long inv;  // round(2^63 / c_j)
+    unsigned long long lnc;  // round(-ln(inv 2^-63) 2^64) = ln c_j to 2^-64
+};
+
+struct LogTable {
+    const LogSlice* slice;       // 256 entries, device memory
+    unsigned long long ln2_q64;  // round(ln 2 * 2^64)
+};
+
+// Table for the current device (built and uploaded on first use; call it
+// outside stream capture before the first launch that needs it).
+mrip_status log_table(LogTable* out);
+
+// -log(K 2^-53) * 2^57 for K in [1, 2^53] (the result is below 53 ln 2 < 2^5.2,
+// so it fits a signed 64-bit word).
+__device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, const LogTable& tab) {
+    const int lz = __clzll(K);
+    const unsigned long long m = K << lz;  // bit 63 set: M = m 2^-63
+    const unsigned long long n = static_cast<unsigned long long>(lz - 10);  // 53 - e
+    const int j = static_cast<int>((m >> 55) & 0xFFu);
+    const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tab.slice) + j);
+    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62
+    const unsigned long long hi = __umul64hi(m, e.x);
+    const unsigned long long lo = m * e.x;
+    const long long R = static_cast<long long>(((hi - (1ULL << 62)) << 2) | (lo >> 62));
+    // Q(r) = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 in Q.63 (|Q| < 0.51)
+    long long q = -1537228672809129301LL;              // -2^63 / 6
+    q = 1844674407370955162LL + __mul64hi(R, q);       //  2^63 / 5
+    q = -2305843009213693952LL + __mul64hi(R, q);      // -2^63 / 4
+    q = 3074457345618258603LL + __mul64hi(R, q);       //  2^63 / 3
+    q = -4611686018427387904LL + __mul64hi(R, q);      // -2^63 / 2
+    const long long r2 = __mul64hi(R, R);              // r^2 2^64
+    const long long l1p = R + 2 * __mul64hi(r2, q);   // log1p(r) 2^64
+    // y 2^57 = n ln2 2^57 - lnc 2^57 - log1p 2^57
+    const unsigned long long p_lo = n * tab.ln2_q64;
+    const unsigned long long p_hi = __umul64hi(n, tab.ln2_q64);
+    const unsigned long long nln2 = (p_hi << 57) | (p_lo >> 7);
+    // near y = 0 (K close to 2^53) the truncations may undershoot: clamp
+    const long long y = static_cast<long long>(nln2 - (e.y >> 7) - static_cast<unsigned long long>(l1p >> 7));
+    return y > 0 ? static_cast<unsigned long long>(y) : 0ULL;
+}
+
+// Exponential variate from words (lo, hi): -log(1 - u) * inv_rate_q57 where
+// inv_rate_q57 = 2^-57 / rate.
+__device__ __forceinline__ double expo_fast(uint32_t lo, uint32_t hi, const LogTable& tab,
+                                            double inv_rate_q57) {
+    const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
+    const unsigned long long K = (1ULL << 53) - (bits >> 11);
+    return __ull2double_rn(neg_log_q57(K, tab)) * inv_rate_q57;
 }
 
 // Bernoulli threshold floor(p 2^32) for p in [0, 1) -- exact in double.

@@ -24,17 +24,19 @@ struct Mm1Out {
 };
 
 // Client n of (dp, rep): service S_n from words (0,1), gap A_{n+1} from (2,3).
-__device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp, double lam,
-                                           double mu, const RoundKeys& rk, double& s, double& a) {
+// inv_mu, inv_lam are 2^-57 / rate (see expo_fast).
+__device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp, double inv_lam,
+                                           double inv_mu, const RoundKeys& rk, const LogTable& tab,
+                                           double& s, double& a) {
     const uint4 b = philox(0u, n, rep, stream_word(0u, dp), rk);
-    s = expo_div(u53(b.x, b.y), mu);
-    a = expo_div(u53(b.z, b.w), lam);
+    s = expo_fast(b.x, b.y, tab, inv_mu);
+    a = expo_fast(b.z, b.w, tab, inv_lam);
 }
 
 template <bool kLane0Only>
 __global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
                                   long long n_reps, long long n_clients,
-                                  const __grid_constant__ RoundKeys rk, Mm1Out out) {
+                                  const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     long long item;
     if (kLane0Only) {
         if ((threadIdx.x & 31) != 0) return;
@@ -45,11 +47,11 @@ __global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_it
     if (item >= n_items) return;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(item % n_reps);
-    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    const double inv_lam = 0x1p-57 / dps[2 * dp], inv_mu = 0x1p-57 / dps[2 * dp + 1];
     double w = 0.0, sum_w = 0.0, sum_i = 0.0, sum_v = 0.0;
     for (long long n = 0; n < n_clients; ++n) {
         double s, a;
-        mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+        mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, s, a);
         sum_w += w;
         const double v = w + s;
         sum_v += v;
@@ -80,7 +82,7 @@ __device__ __forceinline__ MaxPlus compose(MaxPlus f, MaxPlus g) {
 template <bool kStage>
 __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n_items,
                                      long long n_reps, long long n_clients,
-                                     const __grid_constant__ RoundKeys rk, Mm1Out out) {
+                                     const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     extern __shared__ double stage[];  // per warp: S[seg_cap*32], A[seg_cap*32]
     const int lane = threadIdx.x & 31;
     const int warp_in_cta = threadIdx.x >> 5;
@@ -88,7 +90,7 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
     if (item >= n_items) return;  // warp-uniform
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(item % n_reps);
-    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    const double inv_lam = 0x1p-57 / dps[2 * dp], inv_mu = 0x1p-57 / dps[2 * dp + 1];
     const long long seg = (n_clients + 31) / 32;
     const long long lo = lane * seg;
     const long long hi = (lo + seg < n_clients) ? lo + seg : n_clients;
@@ -99,7 +101,7 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
     MaxPlus f{-INFINITY, 0.0};
     for (long long n = lo; n < hi; ++n) {
         double s, a;
-        mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+        mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, s, a);
         if (kStage) {
             s_buf[(n - lo) * 32 + lane] = s;
             a_buf[(n - lo) * 32 + lane] = a;
@@ -130,7 +132,7 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
             s = s_buf[(n - lo) * 32 + lane];
             a = a_buf[(n - lo) * 32 + lane];
         } else {
-            mm1_client(static_cast<uint32_t>(n), rep, dp, lam, mu, rk, s, a);
+            mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, s, a);
         }
         sum_w += w;
         const double v = w + s;
@@ -172,7 +174,8 @@ template <bool kLane0Only>
 __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long n_items,
                                       long long n_reps, long long rep0, long long n_clients,
                                       long long window, uint32_t tag,
-                                      const __grid_constant__ RoundKeys rk, TandemOut out) {
+                                      const __grid_constant__ RoundKeys rk, LogTable tab,
+                                      TandemOut out) {
     long long item;
     if (kLane0Only) {
         if ((threadIdx.x & 31) != 0) return;
@@ -185,6 +188,8 @@ __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long 
     const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const double lam = dps[4 * dp], mu1 = dps[4 * dp + 1], mu2 = dps[4 * dp + 2],
                  mu3 = dps[4 * dp + 3];
+    const double i_lam = 0x1p-57 / lam, i_mu1 = 0x1p-57 / mu1, i_mu2 = 0x1p-57 / mu2,
+                 i_mu3 = 0x1p-57 / mu3;
     const uint32_t c3 = stream_word(tag, dp);
     const long long w_len = (n_clients < window) ? n_clients : window;
     double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
@@ -192,10 +197,10 @@ __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long 
     for (long long n = 0; n < n_clients; ++n) {
         const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
         const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
-        const double a = expo_div(u53(b0.x, b0.y), lam);
-        const double s1 = expo_div(u53(b0.z, b0.w), mu1);
-        const double s2 = expo_div(u53(b1.x, b1.y), mu2);
-        const double s3 = expo_div(u53(b1.z, b1.w), mu3);
+        const double a = expo_fast(b0.x, b0.y, tab, i_lam);
+        const double s1 = expo_fast(b0.z, b0.w, tab, i_mu1);
+        const double s2 = expo_fast(b1.x, b1.y, tab, i_mu2);
+        const double s3 = expo_fast(b1.z, b1.w, tab, i_mu3);
         double q = v1 - a;
         v1 = ((q > 0.0) ? q : 0.0) + s1;
         q = v2 - a;
@@ -243,14 +248,17 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
     if (n_items == 0) return MRIP_OK;
     if (!d_dps) return fail(MRIP_EINVAL, "mrip_mm1_simulate: null design points");
     const RoundKeys rk = expand_key(seed);
+    LogTable tab;
+    mrip_status ts = log_table(&tab);
+    if (ts != MRIP_OK) return ts;
     Mm1Out out{d_wait, d_idle, d_system};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
         mm1_serial_kernel<false><<<ceil_div_u(n_items, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, n_clients, rk, out);
+            d_dps, n_items, n_reps, n_clients, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         mm1_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, n_clients, rk, out);
+            d_dps, n_items, n_reps, n_clients, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_COOP) {
         const long long seg = (n_clients + 31) / 32;
         const size_t per_warp = static_cast<size_t>(seg) * 32 * 2 * sizeof(double);
@@ -262,10 +270,10 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem));
             mm1_warp_coop_kernel<true><<<ceil_div_u(n_items, warps), 32 * warps, smem, st>>>(
-                d_dps, n_items, n_reps, n_clients, rk, out);
+                d_dps, n_items, n_reps, n_clients, rk, tab, out);
         } else {
             mm1_warp_coop_kernel<false><<<ceil_div_u(n_items, 4), 128, 0, st>>>(
-                d_dps, n_items, n_reps, n_clients, rk, out);
+                d_dps, n_items, n_reps, n_clients, rk, tab, out);
         }
     } else {
         return fail(MRIP_EINVAL, "mrip_mm1_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");
@@ -287,14 +295,17 @@ extern "C" mrip_status mrip_tandem3_simulate(const double* d_dps, int32_t n_dp, 
     if (n_items == 0) return MRIP_OK;
     if (!d_dps || !d_y) return fail(MRIP_EINVAL, "mrip_tandem3_simulate: null pointer");
     const RoundKeys rk = expand_key(seed);
+    LogTable tab;
+    mrip_status ts = log_table(&tab);
+    if (ts != MRIP_OK) return ts;
     TandemOut out{d_y, d_feat, n_items};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
         tandem3_serial_kernel<false><<<ceil_div_u(n_items, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, out);
+            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         tandem3_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, out);
+            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, tab, out);
     } else {
         return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD or WARP_1LANE");
     }

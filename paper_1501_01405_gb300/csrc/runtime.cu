@@ -1,6 +1,7 @@
 // Library runtime: thread-local error state, per-device scratch memory,
 // device error flags, and the random-stream stage entry points
 // (mrip_philox, mrip_expo).
+#include <cmath>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -17,6 +18,7 @@ struct DeviceScratch {
     size_t bytes[8] = {0};
     int* flags = nullptr;
     int sms = 0;
+    LogSlice* log_slices = nullptr;
 };
 std::mutex g_scratch_mutex;
 std::vector<DeviceScratch> g_scratch;
@@ -76,6 +78,43 @@ int* device_error_flags() {
     return d.flags;
 }
 
+namespace {
+// 1/c_j and ln c_j for the 256 slices of [1, 2), from the host's long-double
+// logarithm (64-bit or wider mantissa).
+void build_log_slices(std::vector<LogSlice>& t) {
+    t.resize(256);
+    for (int j = 0; j < 256; ++j) {
+        const long double c = 1.0L + (static_cast<long double>(j) + 0.5L) / 256.0L;
+        const unsigned long long inv =
+            static_cast<unsigned long long>(ldexpl(1.0L / c, 63) + 0.5L);
+        const long double ic = ldexpl(static_cast<long double>(inv), -63);
+        const long double lnc = -logl(ic);
+        t[j].inv = inv;
+        t[j].lnc = static_cast<unsigned long long>(ldexpl(lnc, 64) + 0.5L);
+    }
+}
+}  // namespace
+
+mrip_status log_table(LogTable* out) {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    DeviceScratch& d = dev_scratch();
+    if (!d.log_slices) {
+        std::vector<LogSlice> t;
+        build_log_slices(t);
+        LogSlice* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, t.size() * sizeof(LogSlice));
+        if (e == cudaSuccess) e = cudaMemcpy(p, t.data(), t.size() * sizeof(LogSlice), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (p) cudaFree(p);
+            return cuda_status(e, "log table upload");
+        }
+        d.log_slices = p;
+    }
+    out->slice = d.log_slices;
+    out->ln2_q64 = static_cast<unsigned long long>(ldexpl(logl(2.0L), 64) + 0.5L);
+    return MRIP_OK;
+}
+
 int sm_count() {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     DeviceScratch& d = dev_scratch();
@@ -109,12 +148,11 @@ __global__ void philox_kernel(const uint4* __restrict__ ctr, const uint2* __rest
 
 __global__ void expo_kernel(const uint32_t* __restrict__ lo, const uint32_t* __restrict__ hi,
                             const double* __restrict__ rate, long long n, double* __restrict__ u_out,
-                            double* __restrict__ e_out) {
+                            double* __restrict__ e_out, LogTable tab) {
     long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (i >= n) return;
-    double u = u53(lo[i], hi[i]);
-    if (u_out) u_out[i] = u;
-    if (e_out) e_out[i] = expo_div(u, rate[i]);
+    if (u_out) u_out[i] = u53(lo[i], hi[i]);
+    if (e_out) e_out[i] = expo_fast(lo[i], hi[i], tab, 0x1p-57 / rate[i]);
 }
 
 }  // namespace mrip
@@ -142,8 +180,11 @@ extern "C" mrip_status mrip_expo(const uint32_t* d_lo, const uint32_t* d_hi, con
     if (n < 0) return fail(MRIP_EINVAL, "mrip_expo: n < 0");
     if (n == 0) return MRIP_OK;
     if (!d_lo || !d_hi || (d_e && !d_rate)) return fail(MRIP_EINVAL, "mrip_expo: null pointer");
+    LogTable tab;
+    mrip_status s = log_table(&tab);
+    if (s != MRIP_OK) return s;
     expo_kernel<<<ceil_div_u(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        d_lo, d_hi, d_rate, n, d_u, d_e);
+        d_lo, d_hi, d_rate, n, d_u, d_e, tab);
     return launch_status("mrip_expo");
 }
 
