@@ -52,6 +52,11 @@ DFMA_PER_CLK_SM = 2       # FP64 fused multiply-add results (1.25 TFLOP/s nomina
 INT_MULS_PER_PHILOX = 40  # 10 rounds x 2 products x (low + high half)
 
 
+# DRAM bytes (read + write) per launch of a dominant kernel, from the ncu
+# capture summarised in profiles/ (None once the kernel changes).
+PROFILED_TRAFFIC = {"forest_fire_kernel<4>": 36864}
+
+
 def imul_peak_gops():
     return SMS * IMUL_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
 
@@ -290,6 +295,17 @@ class Queue(Workload):
                            threads=threads)
 
 
+def shrink(wl, n):
+    """A smaller case of the same kernel for profiling captures."""
+    w = wl.w
+    if w["dps"].shape[0] > 1 and w.get("kind") == "tandem3":
+        w["dps"] = np.ascontiguousarray(w["dps"][:n])
+        w["n_dp"] = w["dps"].shape[0]
+    else:
+        w["n_reps"] = n
+    wl.w = w
+
+
 def make_workload(name, rank):
     if name in ("ff128", "ff256"):
         return ForestFire(rank, "ff128" if name == "ff128" else "ff256_cv")
@@ -298,6 +314,71 @@ def make_workload(name, rank):
     if name in ("mm1_32", "tandem"):
         return Queue(rank, name)
     raise SystemExit("unknown workload %s" % name)
+
+
+# ---------------------------------------------------------------------------
+# time to a target interval half-width, plain vs learned control variate
+# ---------------------------------------------------------------------------
+CV_DEFAULTS = dict(train_frac=0.1, epochs=20, batch=1024, lr=1e-3)
+
+
+def _median_hw(stats):
+    return float(np.median([s["half_width"] for s in stats]))
+
+
+def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10):
+    """Tandem workload (4,096 design points x 10,000 clients): the target is
+    the median plain 95 % half-width at n_reps replications.  The plain
+    estimator reaches it by definition in the time of that run; the
+    control-variate estimator is run at n_reps, its replication count is
+    scaled by (half-width ratio)^2 to the target, and it is run again at that
+    count, timed end to end (simulation, training, control runs, inference,
+    estimator)."""
+    w = mrip_inputs.workload("tandem_cv")
+    model = eng.Model(eng.MRIP_TANDEM3, n_clients=w["n_clients"], window=w["window"])
+    model.set_stream(stream)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    def cv_run(n):
+        n_train = math.ceil(CV_DEFAULTS["train_frac"] * n)
+        return model.run_cv(w["dps"], n, seed, m_ctrl=m_factor * (n - n_train), **CV_DEFAULTS)
+
+    model.run(w["dps"], n_reps, seed)  # warm (graph capture, allocations)
+    model.stats()
+    _, t_plain = timed(lambda: (model.run(w["dps"], n_reps, seed), model.stats()))
+    plain = model.stats()
+    target = _median_hw(plain)
+    cv_run(n_reps)  # warm
+    (pl, cv, loss), t_cv0 = timed(lambda: cv_run(n_reps))
+    hw0 = _median_hw(cv)
+    n_held0 = cv[0]["n"]
+    n_need = max(n_reps // 8, int(math.ceil(n_held0 * (hw0 / target) ** 2
+                                             / (1 - CV_DEFAULTS["train_frac"]))))
+    (pl2, cv2, loss2), t_cv = timed(lambda: cv_run(n_need))
+    # held-out plain half-width at equal replications (what the network buys)
+    y = model.outputs(0).reshape(w["n_dp"], n_need)
+    n_tr = math.ceil(CV_DEFAULTS["train_frac"] * n_need)
+    ratio = [c["half_width"] / (np.std(y[d, n_tr:], ddof=1) / math.sqrt(n_need - n_tr)
+                                * c["t_crit"]) for d, c in enumerate(cv2)]
+    model.close()
+    return {"workload": ("tandem_cv: 3-station tandem, 4096 design points, 10000 clients, "
+                         "network 8-64-64-1 on 10 percent of replications, "
+                         "{} control runs per held-out replication").format(m_factor),
+            "target_half_width": target,
+            "plain": {"replications": n_reps, "seconds": t_plain,
+                      "median_half_width": target},
+            "cv_at_same_replications": {"replications": n_reps, "seconds": t_cv0,
+                                        "median_half_width": hw0, "train_loss": loss},
+            "cv": {"replications": n_need, "seconds": t_cv,
+                   "median_half_width": _median_hw(cv2), "train_loss": loss2},
+            "cv_over_plain_time": t_cv / t_plain,
+            "median_cv_over_plain_half_width_same_heldout": float(np.median(ratio))}
 
 
 # ---------------------------------------------------------------------------
@@ -426,7 +507,12 @@ def main():
                     choices=["ff128", "ff256", "walk8", "mm1_32", "tandem"])
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-dp", type=int, default=0,
+                    help="profiling only: keep the first N design points (tandem) or use N "
+                         "replications per design point (other workloads)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cv", action="store_true",
+                    help="skip the plain-vs-control-variate time-to-target measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -435,6 +521,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = make_workload(args.workload, rank)
+    if args.n_dp > 0:
+        shrink(wl, args.n_dp)
 
     if args.impl == "reference":
         reference_arm(args, wl, rank, world)
@@ -519,7 +607,8 @@ def main():
     roof = {"bound": rw["bound"], "kernel": rw["kernel"], "achieved": achieved,
             "peak": rw["peak"], "unit": rw["unit"],
             "frac": (achieved / rw["peak"]) if rw["peak"] else None,
-            "traffic": None, "kernel_ms": kmean, "per_unit": rw["per_unit"],
+            "traffic": PROFILED_TRAFFIC.get(rw["kernel"]) if args.n_dp == 0 else None,
+            "kernel_ms": kmean, "per_unit": rw["per_unit"],
             "peak_source": rw["peak_source"]}
 
     line = {"metric": METRIC, "value": value, "unit": "replications/s", "n_gpus": world,
@@ -532,6 +621,8 @@ def main():
             "gpu_launches": wl.launches_per_step * args.steps,
             "wall_s": t_wall}
 
+    if rank == 0 and world == 1 and not args.no_cv:
+        line["time_to_target"] = time_to_target(eng, torch, stream, 42)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = oracle.host_threads()

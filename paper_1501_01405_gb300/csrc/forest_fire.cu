@@ -13,7 +13,14 @@
 // word (i mod 4) of Philox block (c0 = i div 4, c1 = t); for lattice word k
 // that is blocks c0 = 8k .. 8k+7.  A thread compares its 32 cells' words
 // with the growth and lightning thresholds and packs the results into two
-// words; the new state of 32 cells is then a few bitwise operations:
+// words.  The kernel is bound by Philox's 32x32->64 multiplies, which GB300
+// retires at under one warp instruction per SM-clock, so everything else
+// stays off that pipe and the multiplies are trimmed: all blocks of one step
+// share (t, rep, dp), hence round 1's product of counter word 2 and round
+// 2's product of counter word 0 are computed once per step (18 instead of
+// 20 wide multiplies per block, same words).  Lightning is rare: its four
+// compares run only for blocks whose smallest word is below its threshold.
+// The new state of 32 cells is then a few bitwise operations:
 //   ignite = burning neighbour | lightning,
 //   burning' = tree & ignite,
 //   tree'    = (tree & ~ignite) | (empty & grow).
@@ -27,6 +34,41 @@ namespace mrip {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Philox4x32-10 of counter (c0, t, rep, c3) for one step: the parts that do
+// not depend on c0 are precomputed once per step (StepKey).
+struct StepKey {
+    uint32_t x0, x1;      // words 0 and 1 after round 1 (independent of c0)
+    uint32_t p_hi, p_lo;  // round 2's product 0xD2511F53 * x0
+};
+
+__device__ __forceinline__ StepKey step_key(uint32_t t, uint32_t rep, const RoundKeys& rk) {
+    StepKey s;
+    const uint32_t h1 = __umulhi(0xCD9E8D57u, rep);
+    s.x0 = h1 ^ t ^ rk.k0[0];
+    s.x1 = 0xCD9E8D57u * rep;
+    s.p_hi = __umulhi(0xD2511F53u, s.x0);
+    s.p_lo = 0xD2511F53u * s.x0;
+    return s;
+}
+
+__device__ __forceinline__ uint4 philox_step(uint32_t c0, uint32_t c3, const StepKey& sk,
+                                             const RoundKeys& rk) {
+    // round 1: only the product with c0 varies
+    const uint32_t a_hi = __umulhi(0xD2511F53u, c0);
+    const uint32_t a_lo = 0xD2511F53u * c0;
+    const uint32_t w2 = a_hi ^ c3 ^ rk.k1[0];
+    // round 2: the product with word 0 is sk.p
+    const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2);
+    const uint32_t b_lo = 0xCD9E8D57u * w2;
+    uint32_t x0 = b_hi ^ sk.x1 ^ rk.k0[1];
+    uint32_t x1 = b_lo;
+    uint32_t x2 = sk.p_hi ^ a_lo ^ rk.k1[1];
+    uint32_t x3 = sk.p_lo;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) philox_round(x0, x1, x2, x3, rk.k0[r], rk.k1[r]);
+    return make_uint4(x0, x1, x2, x3);
+}
 
 // Threads per CTA for a lattice of W words per row.
 template <int W>
@@ -97,6 +139,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
         uint32_t* nxt_t = lattice + (t & 1) * 2 * NWORD;
         uint32_t* nxt_b = nxt_t + NWORD;
         int c = 0;
+        const StepKey sk = step_key(static_cast<uint32_t>(t), rep, rk);
         for (int k = threadIdx.x; k < NWORD; k += TPB) {
             const int y = k / W;
             const int j = k - y * W;
@@ -110,15 +153,18 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
             uint32_t g = 0, l = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const uint4 b = philox(8u * k + q, static_cast<uint32_t>(t), rep, c3, rk);
+                const uint4 b = philox_step(8u * k + q, c3, sk, rk);
                 g |= (b.x < t_grow) ? (1u << (4 * q)) : 0u;
                 g |= (b.y < t_grow) ? (1u << (4 * q + 1)) : 0u;
                 g |= (b.z < t_grow) ? (1u << (4 * q + 2)) : 0u;
                 g |= (b.w < t_grow) ? (1u << (4 * q + 3)) : 0u;
-                l |= (b.x < t_light) ? (1u << (4 * q)) : 0u;
-                l |= (b.y < t_light) ? (1u << (4 * q + 1)) : 0u;
-                l |= (b.z < t_light) ? (1u << (4 * q + 2)) : 0u;
-                l |= (b.w < t_light) ? (1u << (4 * q + 3)) : 0u;
+                const uint32_t lowest = min(min(b.x, b.y), min(b.z, b.w));
+                if (__builtin_expect(lowest < t_light, 0)) {
+                    l |= (b.x < t_light) ? (1u << (4 * q)) : 0u;
+                    l |= (b.y < t_light) ? (1u << (4 * q + 1)) : 0u;
+                    l |= (b.z < t_light) ? (1u << (4 * q + 2)) : 0u;
+                    l |= (b.w < t_light) ? (1u << (4 * q + 3)) : 0u;
+                }
             }
             const uint32_t ignite = nb | l;
             const uint32_t nbw = tw & ignite;
