@@ -309,6 +309,14 @@ mrip_status mrip_stats_reduce(const double *d_x, int32_t n_dp, int64_t n_reps,
 mrip_status mrip_stats_finalize(const double *nmm2, int32_t n_dp, double conf,
                                 mrip_stat *out);
 
+/* Host, synchronous: merge per-design-point (n, mean, M2) triples of n_parts
+ * disjoint replication sets -- e.g. the shards of several GPUs or a resumed
+ * run -- into one set (Chan, Golub, LeVeque pairwise update, parts merged
+ * in index order, so the result does not depend on arrival order).
+ * parts: host double [n_parts][n_dp][3]; out: host double [n_dp][3].
+ * Empty parts (n = 0) are allowed. */
+mrip_status mrip_stats_merge(const double *parts, int32_t n_parts, int32_t n_dp, double *out);
+
 /* Host: Student-t critical value t with P(T > t) = (1 - conf) / 2, df >= 1. */
 mrip_status mrip_t_crit(double conf, int64_t df, double *out);
 

@@ -147,6 +147,15 @@ def mrip_stats_finalize(nmm2, conf=0.95):
     return [_stat_dict(out[i]) for i in range(n_dp)]
 
 
+def mrip_stats_merge(parts):
+    """Merge (n_parts, n_dp, 3) host triples into (n_dp, 3), parts in order."""
+    a, p = _host(parts, np.float64)
+    a = a.reshape(a.shape[0], -1, 3)
+    out = np.empty((a.shape[1], 3))
+    _check(lib().mrip_stats_merge(p, a.shape[0], a.shape[1], out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
 def mrip_t_crit(conf, df):
     v = ctypes.c_double()
     _check(lib().mrip_t_crit(float(conf), int(df), ctypes.byref(v)))

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_finalize": (_INT, [_P, _I32, _D, _P]),
     "mrip_t_crit": (_INT, [_D, _I64, _P]),
+    "mrip_stats_merge": (_INT, [_P, _I32, _I32, _P]),
     "mrip_mlp_param_count": (_I64, [_I32]),
     "mrip_mlp_init": (_INT, [_I32, _U64, _P, _P]),
     "mrip_mlp_forward": (_INT, [_P, _I32, _P, _I64, _P, _P]),

@@ -242,3 +242,32 @@ extern "C" mrip_status mrip_t_crit(double conf, int64_t df, double* out) {
     *out = t_critical(conf, df);
     return MRIP_OK;
 }
+
+extern "C" mrip_status mrip_stats_merge(const double* parts, int32_t n_parts, int32_t n_dp, double* out) {
+    if (n_parts < 1 || n_dp < 0 || (n_dp > 0 && (!parts || !out)))
+        return fail(MRIP_EINVAL, "mrip_stats_merge: need n_parts >= 1, n_dp >= 0 and buffers");
+    for (int32_t d = 0; d < n_dp; ++d) {
+        double n = 0.0, mean = 0.0, m2 = 0.0;
+        for (int32_t p = 0; p < n_parts; ++p) {
+            const double* t = parts + (static_cast<size_t>(p) * n_dp + d) * 3;
+            const double nb = t[0];
+            if (!(nb >= 0.0)) return fail(MRIP_EINVAL, "mrip_stats_merge: negative count");
+            if (nb == 0.0) continue;
+            if (n == 0.0) {
+                n = nb;
+                mean = t[1];
+                m2 = t[2];
+                continue;
+            }
+            const double tot = n + nb;
+            const double delta = t[1] - mean;
+            mean = mean + delta * (nb / tot);
+            m2 = m2 + t[2] + delta * delta * (n * nb / tot);
+            n = tot;
+        }
+        out[3 * d] = n;
+        out[3 * d + 1] = mean;
+        out[3 * d + 2] = m2;
+    }
+    return MRIP_OK;
+}
