@@ -295,6 +295,91 @@ class Queue(Workload):
                            threads=threads)
 
 
+class AreaWalk(Workload):
+    """The paper's walk (30 areas, 1,000 moves) mapped one replication per thread."""
+    dtype = "i32"
+
+    def __init__(self, rank, n_reps=1 << 16, n_steps=1000, mapping="THREAD"):
+        super().__init__(rank)
+        self.w = dict(n_reps=n_reps, n_steps=n_steps, n_dp=1, dps=np.zeros((1, 1)), kind="area_walk")
+        self.name = "area_walk"
+        self.seed = mrip_inputs.SEED + rank
+        self.mapping = mapping
+
+    def units(self):
+        return self.w["n_reps"]
+
+    def config(self):
+        return {"workload": "area_walk: the paper's 30-area random walk (60x50 periodic map, "
+                            "10x10 areas), %d moves, %d replications" % (self.w["n_steps"], self.w["n_reps"]),
+                "n_reps": self.w["n_reps"], "n_steps": self.w["n_steps"], "seed": self.seed,
+                "mapping": self.mapping}
+
+    def setup(self, eng, torch):
+        self.eng, self.torch = eng, torch
+        n = self.w["n_reps"]
+        self.fa = torch.empty(n, dtype=torch.int32, device="cuda")
+        self.vis = torch.empty(30 * n, dtype=torch.int32, device="cuda")
+
+    def step(self, k_start=None, k_end=None):
+        if k_start is not None:
+            k_start.record()
+        self.eng.mrip_area_walk_simulate(self.w["n_reps"], self.w["n_steps"], self.seed,
+                                         getattr(self.eng, "MRIP_MAP_" + self.mapping), self.fa, self.vis)
+        if k_end is not None:
+            k_end.record()
+
+    launches_per_step = 1
+
+    def roofline_work(self):
+        moves = float(self.w["n_reps"]) * self.w["n_steps"]
+        return dict(kernel="area_walk_serial_kernel", bound="alu", unit="Gop/s (32-bit integer multiply)",
+                    work=moves / 64.0 * INT_MULS_PER_PHILOX, peak=imul_peak_gops(),
+                    peak_source="nominal int-mul rate",
+                    per_unit="40 int multiplies per 64 moves (one Philox block)")
+
+    def make_model(self):
+        return None
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        oracle.area_walk(np.arange(n_items) % self.w["n_reps"], self.w["n_steps"], self.seed,
+                         threads=threads)
+
+
+def area_walk_sweep(eng, torch, n_steps=1000, runs=7):
+    """Time per launch (median of `runs`, CUDA events) of each mapping for
+    1 .. 2^16 replications, and the oracle's time per replication on one
+    core: the GPU-versus-CPU and WLP-versus-TLP comparisons of the paper
+    (Section 5.2-5.3), re-measured."""
+    import oracle
+    out = {"n_steps": n_steps, "reps": [], "ms": {"THREAD": [], "WARP_1LANE": [], "WARP_COOP": []}}
+    maps = list(out["ms"])
+    for k in range(17):
+        n = 1 << k
+        fa = torch.empty(n, dtype=torch.int32, device="cuda")
+        vis = torch.empty(30 * n, dtype=torch.int32, device="cuda")
+        out["reps"].append(n)
+        for mp in maps:
+            times = []
+            for r in range(runs + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                eng.mrip_area_walk_simulate(n, n_steps, 42, getattr(eng, "MRIP_MAP_" + mp), fa, vis)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            out["ms"][mp].append(float(np.median(times)))
+    t0 = time.perf_counter()
+    oracle.area_walk(np.arange(2000), n_steps, 42, threads=1)
+    out["cpu_ms_per_rep_one_core"] = (time.perf_counter() - t0) / 2000 * 1e3
+    i64 = out["reps"].index(64)
+    out["wlp_over_tlp_time_at_64"] = out["ms"]["WARP_1LANE"][i64] / out["ms"]["THREAD"][i64]
+    return out
+
+
 def shrink(wl, n):
     """A smaller case of the same kernel for profiling captures."""
     w = wl.w
@@ -313,6 +398,8 @@ def make_workload(name, rank):
         return Walk(rank)
     if name in ("mm1_32", "tandem"):
         return Queue(rank, name)
+    if name == "area_walk":
+        return AreaWalk(rank)
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -497,6 +584,61 @@ def reference_arm(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def e2e_model(wl, model, stream, torch, steps, barrier, world, total_units):
+    """mrip_run with host design points + mrip_stats reading the intervals back."""
+    import torch.distributed as dist
+    model.set_stream(stream)
+    dps, n_reps = wl.e2e_inputs()
+    for _ in range(3):
+        model.run(dps, n_reps, wl.seed)
+        model.stats(0.95)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        model.run(dps, n_reps, wl.seed)
+        model.stats(0.95)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    model.close()
+    return {"value": total_units / e2e_s, "unit": "replications/s",
+            "h2d_bytes_per_step": int(np.asarray(dps).nbytes),
+            "d2h_bytes_per_step": int(np.asarray(dps).shape[0] * 3 * 8)}
+
+
+def e2e_stage(wl, torch, steps, barrier, world):
+    """Stage entry point per step, then a device-to-host copy of its outputs
+    into pinned memory (the step's result)."""
+    import torch.distributed as dist
+    host_fa = torch.empty(wl.fa.shape, dtype=wl.fa.dtype, pin_memory=True)
+    host_vis = torch.empty(wl.vis.shape, dtype=wl.vis.dtype, pin_memory=True)
+    for _ in range(3):
+        wl.step()
+        host_fa.copy_(wl.fa)
+        host_vis.copy_(wl.vis)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        wl.step()
+        host_fa.copy_(wl.fa)
+        host_vis.copy_(wl.vis)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    return {"seconds": e2e_s, "unit": "replications/s", "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": int(host_fa.numel() * 4 + host_vis.numel() * 4)}
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -504,7 +646,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="ff128",
-                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem"])
+                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem", "area_walk"])
+    ap.add_argument("--sweep", action="store_true",
+                    help="area_walk only: time every mapping for 1 .. 2^16 replications")
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-dp", type=int, default=0,
@@ -540,6 +684,13 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.sweep:
+        if args.workload != "area_walk":
+            raise SystemExit("--sweep applies to --workload area_walk")
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "sweep": area_walk_sweep(eng, torch),
+                              "config": AreaWalk(0).config()}), flush=True)
+        return
     wl.setup(eng, torch)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB > L2
@@ -575,31 +726,14 @@ def main():
     total_units = wl.units() * args.steps * world
     value = total_units / (dev_ms / 1e3)
 
-    # ---- end to end through the model-handle API, host buffers
+    # ---- end to end through the public API, host buffers
     model = wl.make_model()
-    model.set_stream(stream)
-    dps, n_reps = wl.e2e_inputs()
-    for _ in range(3):
-        model.run(dps, n_reps, wl.seed)
-        model.stats(0.95)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        model.run(dps, n_reps, wl.seed)
-        model.stats(0.95)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": total_units / e2e_s, "unit": "replications/s",
-           "h2d_bytes_per_step": int(np.asarray(dps).nbytes),
-           "d2h_bytes_per_step": int(np.asarray(dps).shape[0] * 3 * 8)}
-    model.close()
-
+    if model is None:  # stage entry point: launch, then read the outputs back
+        e2e = e2e_stage(wl, torch, args.steps, barrier, world)
+    else:
+        e2e = e2e_model(wl, model, stream, torch, args.steps, barrier, world, total_units)
+    if model is None:
+        e2e["value"] = total_units / e2e.pop("seconds")
     # ---- roofline of the dominant kernel
     rw = wl.roofline_work()
     kmean = sum(kern_ms) / len(kern_ms)

@@ -295,6 +295,19 @@ mrip_status mrip_walk_simulate_noalloc(const double *radii, int32_t n_dp, int64_
                                        int32_t warps_per_cta, int32_t ctas_per_sm,
                                        int32_t chunk, int64_t *d_tau, void *stream);
 
+/* Area walk: the paper's random-walk model (Section 5.1, third model) and
+ * its WLP-versus-TLP experiment (Section 5.3).  A walker on a 60 x 50
+ * periodic map split into 30 areas of 10 x 10 cells (area x/10 + 6 (y/10))
+ * starts at (30, 25); move m reads field m mod 64 of block (0, m div 64) of
+ * replication `rep`, design point 0 (0:+x 1:-x 2:+y 3:-y); after every move
+ * its area's visit count grows by one.  d_final_area: device int32 n_reps;
+ * d_visits: device int32 30 planes of n_reps (may be NULL).  mapping: THREAD
+ * (one replication per thread), WARP_1LANE (one per warp, lane 0 -- the
+ * paper's WLP) or WARP_COOP (one per warp, lanes share 512-move rounds);
+ * AUTO = THREAD.  n_steps <= 2^30. */
+mrip_status mrip_area_walk_simulate(int64_t n_reps, int32_t n_steps, uint64_t seed, int mapping,
+                                    int32_t *d_final_area, int32_t *d_visits, void *stream);
+
 /* Synchronous.  MRIP_ESTEPCAP if any walk launched since the last check hit
  * its step cap (and clears the flag), else MRIP_OK. */
 mrip_status mrip_check_device_flags(void);

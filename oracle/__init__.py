@@ -62,6 +62,8 @@ def lib():
     L.or_walk_batch.argtypes = [_f64p, _c.c_int64, _i32p, _i64p, _c.c_uint64, _c.c_int64,
                                 _i64p]
     L.or_walk_batch.restype = None
+    L.or_area_walk_batch.argtypes = [_c.c_int64, _i64p, _c.c_int32, _c.c_uint64, _i32p, _i32p]
+    L.or_area_walk_batch.restype = None
     L.or_t_cdf.argtypes = [_c.c_double, _c.c_int64]
     L.or_t_cdf.restype = _c.c_double
     L.or_t_crit.argtypes = [_c.c_double, _c.c_int64]
@@ -227,6 +229,20 @@ def walk(radii, dp_idx, rep_idx, seed, max_steps=1 << 38, threads=1):
                             int(max_steps), tau[lo:hi])
     _run_chunks(run, n, threads)
     return tau
+
+
+def area_walk(rep_idx, n_steps, seed, threads=1):
+    """Area walk per replication: (final area (n,), visits (n, 30))."""
+    rep_idx = np.ascontiguousarray(np.asarray(rep_idx, dtype=np.int64).reshape(-1))
+    n = rep_idx.size
+    final = np.empty(n, np.int32)
+    visits = np.empty((n, 30), np.int32)
+
+    def run(lo, hi):
+        lib().or_area_walk_batch(hi - lo, rep_idx[lo:hi], int(n_steps), int(seed), final[lo:hi],
+                                 visits[lo:hi].reshape(-1))
+    _run_chunks(run, n, threads)
+    return final, visits
 
 
 # ---------------------------------------------------------------------------

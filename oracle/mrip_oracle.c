@@ -555,3 +555,50 @@ void or_expo_batch(int64_t n, const uint32_t *lo, const uint32_t *hi, const doub
         e_out[i] = or_expo(u, rate[i]);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Area walk: the paper's random-walk model (Section 5.1, third model, after
+ * Vattulainen & Ala-Nissila): a walker on a map split into 30 areas; at the
+ * end the walkers are counted per area.  Reading (the paper gives no sizes):
+ * a 60 x 50 periodic map, areas of 10 x 10 cells numbered a = x/10 + 6 (y/10),
+ * start at (30, 25).  Move m reads the same 2-bit field as the L1 walk:
+ * field m mod 64 of block (c0 = 0, c1 = m div 64); 0:+x 1:-x 2:+y 3:-y.
+ * After every move the visit count of the walker's area is incremented.
+ * Outputs: the final area and the 30 visit counts.                        */
+/* ------------------------------------------------------------------------ */
+#define OR_AW_W 60
+#define OR_AW_H 50
+#define OR_AW_CELL 10
+#define OR_AW_AREAS 30
+
+void or_area_walk_rep(int32_t n_steps, uint64_t seed, uint32_t rep, int32_t *final_area,
+                      int32_t visits[30])
+{
+    int32_t x = OR_AW_W / 2, y = OR_AW_H / 2;
+    uint32_t blk[4];
+    for (int a = 0; a < OR_AW_AREAS; ++a)
+        visits[a] = 0;
+    for (int32_t m = 0; m < n_steps; ++m) {
+        if ((m & 63) == 0)
+            or_block(seed, 0u, 0u, rep, (uint32_t)(m >> 6), 0u, blk);
+        int k = m & 63;
+        uint32_t field = (blk[k >> 4] >> (2 * (k & 15))) & 3u;
+        if (field == 0)
+            x = (x + 1) % OR_AW_W;
+        else if (field == 1)
+            x = (x + OR_AW_W - 1) % OR_AW_W;
+        else if (field == 2)
+            y = (y + 1) % OR_AW_H;
+        else
+            y = (y + OR_AW_H - 1) % OR_AW_H;
+        visits[x / OR_AW_CELL + (OR_AW_W / OR_AW_CELL) * (y / OR_AW_CELL)] += 1;
+    }
+    *final_area = x / OR_AW_CELL + (OR_AW_W / OR_AW_CELL) * (y / OR_AW_CELL);
+}
+
+void or_area_walk_batch(int64_t n_items, const int64_t *rep_idx, int32_t n_steps, uint64_t seed,
+                        int32_t *final_area, int32_t *visits /* n_items x 30 */)
+{
+    for (int64_t i = 0; i < n_items; ++i)
+        or_area_walk_rep(n_steps, seed, (uint32_t)rep_idx[i], &final_area[i], visits + 30 * i);
+}

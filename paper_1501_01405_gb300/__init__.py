@@ -129,6 +129,13 @@ def mrip_walk_simulate_noalloc(radii, n_reps, seed, max_steps, mapping, tau, war
                                             _stream(stream)))
 
 
+def mrip_area_walk_simulate(n_reps, n_steps, seed, mapping, final_area, visits=None, stream=None):
+    t = _t()
+    _check(lib().mrip_area_walk_simulate(int(n_reps), int(n_steps), int(seed), int(mapping),
+                                         _dev(final_area, t.int32, "final_area"),
+                                         _dev(visits, t.int32, allow_none=True), _stream(stream)))
+
+
 def mrip_check_device_flags():
     _check(lib().mrip_check_device_flags())
 

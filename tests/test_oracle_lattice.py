@@ -201,3 +201,48 @@ def test_walk_parity_large_radius_and_cap():
         assert 0.4 * R * R < tau[dp == d].mean() < 1.0 * R * R
     capped = oracle.walk([64.0], [0], [0], 42, max_steps=10)
     assert capped[0] == -1
+
+
+# ---------------------------------------------------------------- area walk
+def _area_walk_exact(n_steps, W=60, Hh=50, cell=10):
+    """Exact position law of the walk on the W x H torus by dynamic
+    programming; returns (final-area probabilities, expected visits)."""
+    p = np.zeros((Hh, W))
+    p[Hh // 2, W // 2] = 1.0
+    area = (np.arange(W)[None, :] // cell) + (W // cell) * (np.arange(Hh)[:, None] // cell)
+    visits = np.zeros(30)
+    for _ in range(n_steps):
+        p = 0.25 * (np.roll(p, 1, 1) + np.roll(p, -1, 1) + np.roll(p, 1, 0) + np.roll(p, -1, 0))
+        visits += np.bincount(area.ravel(), weights=p.ravel(), minlength=30)
+    final = np.bincount(area.ravel(), weights=p.ravel(), minlength=30)
+    return final, visits
+
+
+def test_area_walk_counts_and_exact_law():
+    n, steps = 20000, 1000
+    final, visits = oracle.area_walk(np.arange(n), steps, 42, threads=oracle.host_threads())
+    assert np.all(visits.sum(axis=1) == steps)
+    assert final.min() >= 0 and final.max() < 30
+    p_final, e_visits = _area_walk_exact(steps)
+    assert p_final.sum() == pytest.approx(1.0, abs=1e-12)
+    hist = np.bincount(final, minlength=30).astype(float)
+    exp = p_final * n
+    keep = exp >= 5
+    obs = np.append(hist[keep], hist[~keep].sum())
+    ex = np.append(exp[keep], n - exp[keep].sum())
+    assert stats.chisquare(obs, ex).pvalue > 1e-4
+    # mean visit counts per area against the exact expectation
+    m = visits.mean(axis=0)
+    se = visits.std(axis=0, ddof=1) / math.sqrt(n)
+    z = np.abs(m - e_visits) / np.maximum(se, 1e-12)
+    assert np.all(z[se > 0] < 5) and np.all(m[se == 0] == e_visits[se == 0].round())
+
+
+def test_area_walk_one_step_and_long_run_uniformity():
+    final, visits = oracle.area_walk(np.arange(400), 1, 7)
+    # one move from (30, 25) stays in area 3 + 6*2 = 15 unless it leaves the block
+    assert set(np.unique(final)) <= {14, 15}
+    n, steps = 64, 200000
+    _, visits = oracle.area_walk(np.arange(n), steps, 3, threads=oracle.host_threads())
+    frac = visits.sum(axis=0) / (n * steps)
+    assert np.all(np.abs(frac - 1 / 30) < 0.012)  # stationary law: uniform over the torus

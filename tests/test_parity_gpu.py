@@ -408,3 +408,20 @@ def test_errors_do_not_poison_the_context(eng, torch_mod):
     m.run(np.array([[0.5, 1.0]]), 4, 1)
     assert m.stats()[0]["n"] == 4
     m.close()
+
+
+# ------------------------------------------------------------------ area walk
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP"])
+@pytest.mark.parametrize("n_steps", [0, 1, 17, 1000, 1537])
+def test_area_walk_all_mappings_bit_exact(eng, torch_mod, mapping, n_steps):
+    t = torch_mod
+    n = 301
+    fa = t.full((n,), -1, dtype=t.int32, device="cuda")
+    vis = t.full((30 * n,), -1, dtype=t.int32, device="cuda")
+    eng.mrip_area_walk_simulate(n, n_steps, 42, getattr(eng, "MRIP_MAP_" + mapping), fa, vis)
+    ref_f, ref_v = oracle.area_walk(np.arange(n), n_steps, 42, threads=threads())
+    if n_steps > 0:
+        assert np.array_equal(fa.cpu().numpy(), ref_f)
+    else:
+        assert np.all(fa.cpu().numpy() == 15)
+    assert np.array_equal(vis.cpu().numpy().reshape(30, n).T, ref_v)
