@@ -341,10 +341,118 @@ class AreaWalk(Workload):
     def make_model(self):
         return None
 
+    def outputs(self):
+        return [self.fa, self.vis]
+
     def oracle_sample(self, n_items, threads):
         import oracle
         oracle.area_walk(np.arange(n_items) % self.w["n_reps"], self.w["n_steps"], self.seed,
                          threads=threads)
+
+
+class MonteCarloPi(Workload):
+    """The paper's first model: pi from the share of 10^7 random points per
+    replication that fall in the quarter disc; 256 replications."""
+    dtype = "u32"
+
+    def __init__(self, rank, n_reps=256, n_draws=10**7):
+        super().__init__(rank)
+        self.w = dict(n_reps=n_reps, n_draws=n_draws, n_dp=1, dps=np.zeros((1, 1)), kind="pi")
+        self.name = "pi"
+        self.seed = mrip_inputs.SEED + rank
+
+    def units(self):
+        return self.w["n_reps"]
+
+    def config(self):
+        return {"workload": "pi: Monte Carlo pi, %d draws per replication, %d replications"
+                            % (self.w["n_draws"], self.w["n_reps"]),
+                "n_reps": self.w["n_reps"], "n_draws": self.w["n_draws"], "seed": self.seed}
+
+    def setup(self, eng, torch):
+        self.eng, self.torch = eng, torch
+        self.hits = torch.empty(self.w["n_reps"], dtype=torch.int64, device="cuda")
+
+    def step(self, k_start=None, k_end=None):
+        if k_start is not None:
+            k_start.record()
+        self.eng.mrip_pi_simulate(self.w["n_reps"], self.w["n_draws"], self.seed, self.hits)
+        if k_end is not None:
+            k_end.record()
+
+    launches_per_step = 1  # plus the clearing memset of the counters
+
+    def roofline_work(self):
+        draws = float(self.w["n_reps"]) * self.w["n_draws"]
+        return dict(kernel="pi_kernel", bound="alu", unit="Gop/s (32-bit integer multiply)",
+                    work=draws * (INT_MULS_PER_PHILOX + 4) / 2.0, peak=imul_peak_gops(),
+                    peak_source="nominal int-mul rate",
+                    per_unit="22 int multiplies per draw (half a Philox block + two 32x32->64 squares)")
+
+    def make_model(self):
+        return None
+
+    def outputs(self):
+        return [self.hits]
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        oracle.pi_hits(np.arange(n_items) % self.w["n_reps"], self.w["n_draws"], self.seed, threads=threads)
+
+
+def pi_sweep(eng, torch, n_draws=10**7, runs=7):
+    """Time per launch (median of `runs`, CUDA events) for 1 .. 256
+    replications of 10^7 draws, and the oracle's time per replication on one
+    core: the paper's GPU-versus-CPU curve for this model (Section 5.2)."""
+    import oracle
+    out = {"n_draws": n_draws, "reps": [], "ms": []}
+    for n in list(range(1, 9)) + [16, 32, 64, 65, 128, 152, 153, 256]:
+        hits = torch.empty(n, dtype=torch.int64, device="cuda")
+        times = []
+        for r in range(runs + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            eng.mrip_pi_simulate(n, n_draws, 42, hits)
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+        out["reps"].append(n)
+        out["ms"].append(float(np.median(times)))
+    t0 = time.perf_counter()
+    oracle.pi_hits(np.arange(4), n_draws, 42, threads=1)
+    out["cpu_ms_per_rep_one_core"] = (time.perf_counter() - t0) / 4 * 1e3
+    return out
+
+
+def tandem_sweep(eng, torch, n_clients=10**5, runs=5):
+    """Few replications of a long horizon: time per launch (median of `runs`,
+    CUDA events) of each tandem mapping for 1 .. 16,384 replications of
+    10^5 clients at one design point (lambda 0.9, mu 1.0, 1.1, 1.2)."""
+    out = {"n_clients": n_clients, "reps": [], "ms": {"THREAD": [], "WARP_1LANE": [], "WARP_COOP": []}}
+    dps = torch.tensor([[0.9, 1.0, 1.1, 1.2]], dtype=torch.float64, device="cuda")
+    for k in range(0, 15, 2):
+        n = 1 << k
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        out["reps"].append(n)
+        for mp in out["ms"]:
+            if mp == "WARP_1LANE" and n > 1024:
+                out["ms"][mp].append(None)
+                continue
+            times = []
+            for r in range(runs + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                eng.mrip_tandem3_simulate(dps, 0, n, n_clients, 100, 42, 0, getattr(eng, "MRIP_MAP_" + mp),
+                                          y, None)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            out["ms"][mp].append(float(np.median(times)))
+    return out
 
 
 def area_walk_sweep(eng, torch, n_steps=1000, runs=7):
@@ -400,6 +508,8 @@ def make_workload(name, rank):
         return Queue(rank, name)
     if name == "area_walk":
         return AreaWalk(rank)
+    if name == "pi":
+        return MonteCarloPi(rank)
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -615,19 +725,19 @@ def e2e_stage(wl, torch, steps, barrier, world):
     """Stage entry point per step, then a device-to-host copy of its outputs
     into pinned memory (the step's result)."""
     import torch.distributed as dist
-    host_fa = torch.empty(wl.fa.shape, dtype=wl.fa.dtype, pin_memory=True)
-    host_vis = torch.empty(wl.vis.shape, dtype=wl.vis.dtype, pin_memory=True)
+    dev = wl.outputs()
+    host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in dev]
     for _ in range(3):
         wl.step()
-        host_fa.copy_(wl.fa)
-        host_vis.copy_(wl.vis)
+        for h, d in zip(host, dev):
+            h.copy_(d)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         wl.step()
-        host_fa.copy_(wl.fa)
-        host_vis.copy_(wl.vis)
+        for h, d in zip(host, dev):
+            h.copy_(d)
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
@@ -636,7 +746,7 @@ def e2e_stage(wl, torch, steps, barrier, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     return {"seconds": e2e_s, "unit": "replications/s", "h2d_bytes_per_step": 0,
-            "d2h_bytes_per_step": int(host_fa.numel() * 4 + host_vis.numel() * 4)}
+            "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host))}
 
 
 # ---------------------------------------------------------------------------
@@ -646,9 +756,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="ff128",
-                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem", "area_walk"])
+                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem", "area_walk", "pi"])
     ap.add_argument("--sweep", action="store_true",
-                    help="area_walk only: time every mapping for 1 .. 2^16 replications")
+                    help="area_walk: time every mapping for 1 .. 2^16 replications; "
+                         "pi: time 1 .. 256 replications; tandem: mappings for 1 .. 16,384 "
+                         "replications of 10^5 clients")
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-dp", type=int, default=0,
@@ -685,11 +797,12 @@ def main():
             dist.barrier()
 
     if args.sweep:
-        if args.workload != "area_walk":
-            raise SystemExit("--sweep applies to --workload area_walk")
+        sweeps = {"area_walk": area_walk_sweep, "pi": pi_sweep, "tandem": tandem_sweep}
+        if args.workload not in sweeps:
+            raise SystemExit("--sweep applies to --workload area_walk, pi or tandem")
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "sweep": area_walk_sweep(eng, torch),
-                              "config": AreaWalk(0).config()}), flush=True)
+            print(json.dumps({"metric": METRIC, "sweep": sweeps[args.workload](eng, torch),
+                              "config": wl.config()}), flush=True)
         return
     wl.setup(eng, torch)
     stream = torch.cuda.current_stream()

@@ -238,7 +238,11 @@ mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
  * rep0 .. rep0 + n_reps - 1 of stream `tag`.  d_y: device n_dp * n_reps;
  * d_feat (may be NULL): device 8 planes of n_dp * n_reps: lambda, mu1..3 and
  * the means over the first min(window, n_clients) clients of A, S1, S2, S3.
- * If n_clients == window only the early window is simulated (control runs). */
+ * If n_clients == window only the early window is simulated (control runs).
+ * mapping: THREAD, WARP_1LANE or WARP_COOP (one replication per warp: lanes
+ * take 32 contiguous client segments, a warp scan of their max-plus maps gives
+ * each segment's entry state; for few replications of many clients).
+ * AUTO = THREAD. */
 mrip_status mrip_tandem3_simulate(const double *d_dps, int32_t n_dp, int64_t rep0,
                                   int64_t n_reps, int64_t n_clients, int64_t window,
                                   uint64_t seed, uint32_t tag, int mapping, double *d_y,
@@ -307,6 +311,14 @@ mrip_status mrip_walk_simulate_noalloc(const double *radii, int32_t n_dp, int64_
  * AUTO = THREAD.  n_steps <= 2^30. */
 mrip_status mrip_area_walk_simulate(int64_t n_reps, int32_t n_steps, uint64_t seed, int mapping,
                                     int32_t *d_final_area, int32_t *d_visits, void *stream);
+
+/* Monte Carlo pi (paper, Section 5.1, first model).  Draw k of replication
+ * `rep` (design point 0) uses words 2(k mod 2), 2(k mod 2)+1 of block
+ * (0, k div 2) as integers x, y in [0, 2^32); it hits iff x^2 + y^2 < 2^64.
+ * d_hits: device int64 n_reps (cleared, then filled with the hit counts;
+ * pi ~ 4 hits / n_draws).  n_draws <= 2^33. */
+mrip_status mrip_pi_simulate(int64_t n_reps, int64_t n_draws, uint64_t seed, int64_t *d_hits,
+                             void *stream);
 
 /* Synchronous.  MRIP_ESTEPCAP if any walk launched since the last check hit
  * its step cap (and clears the flag), else MRIP_OK. */

@@ -64,6 +64,8 @@ def lib():
     L.or_walk_batch.restype = None
     L.or_area_walk_batch.argtypes = [_c.c_int64, _i64p, _c.c_int32, _c.c_uint64, _i32p, _i32p]
     L.or_area_walk_batch.restype = None
+    L.or_pi_batch.argtypes = [_c.c_int64, _i64p, _c.c_int64, _c.c_uint64, _i64p]
+    L.or_pi_batch.restype = None
     L.or_t_cdf.argtypes = [_c.c_double, _c.c_int64]
     L.or_t_cdf.restype = _c.c_double
     L.or_t_crit.argtypes = [_c.c_double, _c.c_int64]
@@ -243,6 +245,17 @@ def area_walk(rep_idx, n_steps, seed, threads=1):
                                  visits[lo:hi].reshape(-1))
     _run_chunks(run, n, threads)
     return final, visits
+
+
+def pi_hits(rep_idx, n_draws, seed, threads=1):
+    """Monte Carlo pi per replication: number of the n_draws points inside."""
+    rep_idx = np.ascontiguousarray(np.asarray(rep_idx, dtype=np.int64).reshape(-1))
+    hits = np.empty(rep_idx.size, np.int64)
+
+    def run(lo, hi):
+        lib().or_pi_batch(hi - lo, rep_idx[lo:hi], int(n_draws), int(seed), hits[lo:hi])
+    _run_chunks(run, rep_idx.size, threads)
+    return hits
 
 
 # ---------------------------------------------------------------------------

@@ -602,3 +602,33 @@ void or_area_walk_batch(int64_t n_items, const int64_t *rep_idx, int32_t n_steps
     for (int64_t i = 0; i < n_items; ++i)
         or_area_walk_rep(n_steps, seed, (uint32_t)rep_idx[i], &final_area[i], visits + 30 * i);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Monte Carlo pi (paper, Section 5.1, first model): random points in the
+ * unit square, counted when they fall in the quarter disc; pi is estimated
+ * by 4 hits / draws.  Draw k uses words 2(k mod 2) and 2(k mod 2)+1 of block
+ * (c0 = 0, c1 = k div 2) as integer coordinates x, y in [0, 2^32); the
+ * point is inside iff x^2 + y^2 < 2^64 (exact in integers).  Output: hits. */
+/* ------------------------------------------------------------------------ */
+int64_t or_pi_rep(int64_t n_draws, uint64_t seed, uint32_t rep)
+{
+    int64_t hits = 0;
+    uint32_t blk[4];
+    for (int64_t k = 0; k < n_draws; ++k) {
+        if ((k & 1) == 0)
+            or_block(seed, 0u, 0u, rep, (uint32_t)(k >> 1), 0u, blk);
+        uint64_t x = blk[2 * (k & 1)], y = blk[2 * (k & 1) + 1];
+        uint64_t x2 = x * x, y2 = y * y;
+        /* x^2 + y^2 < 2^64  <=>  x^2 <= 2^64 - 1 - y^2 */
+        if (x2 <= UINT64_MAX - y2)
+            ++hits;
+    }
+    return hits;
+}
+
+void or_pi_batch(int64_t n_items, const int64_t *rep_idx, int64_t n_draws, uint64_t seed,
+                 int64_t *hits)
+{
+    for (int64_t i = 0; i < n_items; ++i)
+        hits[i] = or_pi_rep(n_draws, seed, (uint32_t)rep_idx[i]);
+}

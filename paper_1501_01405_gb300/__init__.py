@@ -136,6 +136,12 @@ def mrip_area_walk_simulate(n_reps, n_steps, seed, mapping, final_area, visits=N
                                          _dev(visits, t.int32, allow_none=True), _stream(stream)))
 
 
+def mrip_pi_simulate(n_reps, n_draws, seed, hits, stream=None):
+    t = _t()
+    _check(lib().mrip_pi_simulate(int(n_reps), int(n_draws), int(seed), _dev(hits, t.int64, "hits"),
+                                  _stream(stream)))
+
+
 def mrip_check_device_flags():
     _check(lib().mrip_check_device_flags())
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "mrip_walk_simulate_noalloc": (_INT, [_P, _I32, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P,
                                           _P]),
     "mrip_area_walk_simulate": (_INT, [_I64, _I32, _U64, _INT, _P, _P, _P]),
+    "mrip_pi_simulate": (_INT, [_I64, _I64, _U64, _P, _P]),
     "mrip_check_device_flags": (_INT, []),
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_finalize": (_INT, [_P, _I32, _D, _P]),

@@ -124,7 +124,7 @@ def test_tandem_thread_and_wlp(eng, torch_mod):
     n_reps, n_clients, window = 7, 2000, 100
     ref_y, ref_f = oracle.tandem3(dps, *oracle.all_items(5, n_reps), n_clients, 42,
                                   window=window, threads=threads())
-    for mapping in (eng.MRIP_MAP_THREAD, eng.MRIP_MAP_WARP_1LANE):
+    for mapping in (eng.MRIP_MAP_THREAD, eng.MRIP_MAP_WARP_1LANE, eng.MRIP_MAP_WARP_COOP):
         y = t.empty(5 * n_reps, dtype=t.float64, device="cuda")
         f = t.empty(8 * 5 * n_reps, dtype=t.float64, device="cuda")
         eng.mrip_tandem3_simulate(dev(t, dps), 0, n_reps, n_clients, window, 42, 0, mapping, y, f)
@@ -146,6 +146,25 @@ def test_tandem_offset_tag_and_short_runs(eng, torch_mod):
     # fewer clients than the window
     eng.mrip_tandem3_simulate(dev(t, dps), 0, 9, 7, 100, 42, 0, eng.MRIP_MAP_THREAD, y, f)
     ry, rf = oracle.tandem3(dps, *oracle.all_items(3, 9), 7, 42, window=100)
+    np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
+
+
+@pytest.mark.parametrize("n_clients,window", [(1, 1), (31, 5), (33, 100), (1000, 64), (100003, 4096)])
+def test_tandem_warp_coop_ragged(eng, torch_mod, n_clients, window):
+    """Warp scan over 32 client segments: fewer clients than lanes, a
+    ragged last segment, window shorter and longer than a segment, a long
+    horizon; offset replications and a non-zero stream tag."""
+    t = torch_mod
+    dps = mrip_inputs.tandem_design_points(3, seed=11)
+    n_reps, rep0 = 4, 3
+    dp, rep = oracle.all_items(3, n_reps)
+    ry, rf = oracle.tandem3(dps, dp, rep + rep0, n_clients, 42, window=window, tag=2,
+                            threads=threads())
+    y = t.empty(3 * n_reps, dtype=t.float64, device="cuda")
+    f = t.empty(8 * 3 * n_reps, dtype=t.float64, device="cuda")
+    eng.mrip_tandem3_simulate(dev(t, dps), rep0, n_reps, n_clients, window, 42, 2,
+                              eng.MRIP_MAP_WARP_COOP, y, f)
+    np.testing.assert_allclose(y.cpu().numpy(), ry, rtol=REL)
     np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
 
 
@@ -425,3 +444,14 @@ def test_area_walk_all_mappings_bit_exact(eng, torch_mod, mapping, n_steps):
     else:
         assert np.all(fa.cpu().numpy() == 15)
     assert np.array_equal(vis.cpu().numpy().reshape(30, n).T, ref_v)
+
+
+# ------------------------------------------------------------------ Monte Carlo pi
+@pytest.mark.parametrize("n_draws", [0, 1, 2, 3, 65535, 65536, 65537, 10**7])
+def test_pi_bit_exact(eng, torch_mod, n_draws):
+    t = torch_mod
+    reps = 5 if n_draws < 10**7 else 3
+    hits = t.full((reps,), -1, dtype=t.int64, device="cuda")
+    eng.mrip_pi_simulate(reps, n_draws, 42, hits)
+    ref = oracle.pi_hits(np.arange(reps), n_draws, 42, threads=threads())
+    assert np.array_equal(hits.cpu().numpy(), ref)
