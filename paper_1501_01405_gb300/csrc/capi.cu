@@ -290,7 +290,8 @@ bool mapping_allowed(int kind, int mapping) {
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD ||
                    mapping == MRIP_MAP_WARP_1LANE || mapping == MRIP_MAP_WARP_COOP;
         case MRIP_TANDEM3:
-            return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE;
+            return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE ||
+                   mapping == MRIP_MAP_WARP_COOP;
         case MRIP_FOREST_FIRE: return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_CTA;
         case MRIP_WALK_L1_EXIT:
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE ||
@@ -317,6 +318,7 @@ std::vector<Plan> candidates(int kind) {
             break;
         case MRIP_TANDEM3:
             add(MRIP_MAP_THREAD, 0, 0, 0);
+            add(MRIP_MAP_WARP_COOP, 0, 0, 0);
             add(MRIP_MAP_WARP_1LANE, 0, 0, 0);
             break;
         case MRIP_FOREST_FIRE: add(MRIP_MAP_CTA, 0, 0, 0); break;

@@ -9,7 +9,8 @@
 //               composes to maps W -> max(c, W + d); lanes compose their
 //               segment's map, a warp scan of the maps gives each segment's
 //               entry wait, and each lane then replays its segment with the
-//               plain recurrence.
+//               plain recurrence.  The tandem does the same with 3-station
+//               max-plus maps (lower-triangular 3x3 matrix plus constants).
 #include "common.cuh"
 
 namespace mrip {
@@ -231,6 +232,172 @@ __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long 
     }
 }
 
+// Tandem, one warp per replication.  One client maps the arrival-relative
+// state v = (v1, v2, v3) to v'_j = max(v_j - A, v'_{j-1}) + S_j (v'_0 = 0),
+// a max-plus affine map with a lower-triangular matrix:
+//   v'_j = max(c_j, max_{k <= j} (v_k + d_jk)).
+// Maps compose (TMap below), so a warp scan over the lanes' segment maps gives
+// each segment's entry state (the composed map applied to the empty state,
+// i.e. its constant terms c); every lane then replays its segment with the
+// plain recurrence, as the serial kernel does.
+struct TMap {
+    double c1, c2, c3, d11, d21, d22, d31, d32, d33;
+};
+
+__device__ __forceinline__ TMap tmap_identity() {
+    return TMap{-INFINITY, -INFINITY, -INFINITY, 0.0, -INFINITY, 0.0, -INFINITY, -INFINITY, 0.0};
+}
+
+__device__ __forceinline__ double dmax(double x, double y) { return x > y ? x : y; }
+
+// f followed by one client (a, s1, s2, s3)
+__device__ __forceinline__ TMap tmap_push(const TMap& f, double a, double s1, double s2, double s3) {
+    const double e1 = s1 - a, e2 = s2 - a, e3 = s3 - a;
+    TMap r;
+    r.c1 = dmax(s1, f.c1 + e1);
+    r.d11 = f.d11 + e1;
+    r.c2 = dmax(f.c2 + e2, r.c1 + s2);
+    r.d21 = dmax(f.d21 + e2, r.d11 + s2);
+    r.d22 = f.d22 + e2;
+    r.c3 = dmax(f.c3 + e3, r.c2 + s3);
+    r.d31 = dmax(f.d31 + e3, r.d21 + s3);
+    r.d32 = dmax(f.d32 + e3, r.d22 + s3);
+    r.d33 = f.d33 + e3;
+    return r;
+}
+
+// g after f
+__device__ __forceinline__ TMap tmap_compose(const TMap& f, const TMap& g) {
+    TMap h;
+    h.c1 = dmax(g.c1, f.c1 + g.d11);
+    h.c2 = dmax(g.c2, dmax(f.c1 + g.d21, f.c2 + g.d22));
+    h.c3 = dmax(g.c3, dmax(f.c1 + g.d31, dmax(f.c2 + g.d32, f.c3 + g.d33)));
+    h.d11 = f.d11 + g.d11;
+    h.d21 = dmax(f.d11 + g.d21, f.d21 + g.d22);
+    h.d22 = f.d22 + g.d22;
+    h.d31 = dmax(f.d11 + g.d31, dmax(f.d21 + g.d32, f.d31 + g.d33));
+    h.d32 = dmax(f.d22 + g.d32, f.d32 + g.d33);
+    h.d33 = f.d33 + g.d33;
+    return h;
+}
+
+__device__ __forceinline__ TMap tmap_shfl_up(const TMap& m, int off) {
+    TMap r;
+    r.c1 = __shfl_up_sync(kFull, m.c1, off);
+    r.c2 = __shfl_up_sync(kFull, m.c2, off);
+    r.c3 = __shfl_up_sync(kFull, m.c3, off);
+    r.d11 = __shfl_up_sync(kFull, m.d11, off);
+    r.d21 = __shfl_up_sync(kFull, m.d21, off);
+    r.d22 = __shfl_up_sync(kFull, m.d22, off);
+    r.d31 = __shfl_up_sync(kFull, m.d31, off);
+    r.d32 = __shfl_up_sync(kFull, m.d32, off);
+    r.d33 = __shfl_up_sync(kFull, m.d33, off);
+    return r;
+}
+
+struct TandemClient {
+    double a, s1, s2, s3;
+};
+
+__device__ __forceinline__ TandemClient tandem_client(uint32_t n, uint32_t rep, uint32_t c3,
+                                                      const RoundKeys& rk, const LogTable& tab,
+                                                      double i_lam, double i_mu1, double i_mu2,
+                                                      double i_mu3) {
+    const uint4 b0 = philox(0u, n, rep, c3, rk);
+    const uint4 b1 = philox(1u, n, rep, c3, rk);
+    return TandemClient{expo_fast(b0.x, b0.y, tab, i_lam), expo_fast(b0.z, b0.w, tab, i_mu1),
+                        expo_fast(b1.x, b1.y, tab, i_mu2), expo_fast(b1.z, b1.w, tab, i_mu3)};
+}
+
+__global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
+    const double* __restrict__ dps, long long n_items, long long n_reps, long long rep0,
+    long long n_clients, long long window, uint32_t tag, const __grid_constant__ RoundKeys rk,
+    LogTable tab, TandemOut out) {
+    const int lane = threadIdx.x & 31;
+    const long long item = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
+    if (item >= n_items) return;  // warp-uniform
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
+    const double lam = dps[4 * dp], mu1 = dps[4 * dp + 1], mu2 = dps[4 * dp + 2], mu3 = dps[4 * dp + 3];
+    const double i_lam = 0x1p-57 / lam, i_mu1 = 0x1p-57 / mu1, i_mu2 = 0x1p-57 / mu2,
+                 i_mu3 = 0x1p-57 / mu3;
+    const uint32_t c3 = stream_word(tag, dp);
+    const long long w_len = (n_clients < window) ? n_clients : window;
+    const long long seg = (n_clients + 31) / 32;
+    const long long lo = min(lane * seg, n_clients);
+    const long long hi = min(lo + seg, n_clients);
+
+    // pass 1: this segment's map
+    TMap f = tmap_identity();
+    for (long long n = lo; n < hi; ++n) {
+        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
+        f = tmap_push(f, k.a, k.s1, k.s2, k.s3);
+    }
+    // inclusive scan over lanes, then the previous lane's prefix is the entry map
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const TMap prev = tmap_shfl_up(f, off);
+        if (lane >= off) f = tmap_compose(prev, f);
+    }
+    const TMap excl = tmap_shfl_up(f, 1);
+    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
+    if (lane > 0) {
+        v1 = excl.c1;
+        v2 = excl.c2;
+        v3 = excl.c3;
+    }
+
+    // pass 2: replay the segment with the plain recurrence
+    double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
+    for (long long n = lo; n < hi; ++n) {
+        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
+        double q = v1 - k.a;
+        v1 = ((q > 0.0) ? q : 0.0) + k.s1;
+        q = v2 - k.a;
+        v2 = ((q > v1) ? q : v1) + k.s2;
+        q = v3 - k.a;
+        v3 = ((q > v2) ? q : v2) + k.s3;
+        sum_y += v3;
+        if (n < w_len) {
+            sum_a += k.a;
+            sum_1 += k.s1;
+            sum_2 += k.s2;
+            sum_3 += k.s3;
+        }
+    }
+    // fixed-order (lane-ordered tree) reduction
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double oy = __shfl_down_sync(kFull, sum_y, off);
+        const double oa = __shfl_down_sync(kFull, sum_a, off);
+        const double o1 = __shfl_down_sync(kFull, sum_1, off);
+        const double o2 = __shfl_down_sync(kFull, sum_2, off);
+        const double o3 = __shfl_down_sync(kFull, sum_3, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            sum_y += oy;
+            sum_a += oa;
+            sum_1 += o1;
+            sum_2 += o2;
+            sum_3 += o3;
+        }
+    }
+    if (lane != 0) return;
+    out.y[item] = sum_y / static_cast<double>(n_clients);
+    if (out.feat) {
+        const double wl = static_cast<double>(w_len);
+        double* fo = out.feat + item;
+        const long long p = out.plane;
+        fo[0] = lam;
+        fo[p] = mu1;
+        fo[2 * p] = mu2;
+        fo[3 * p] = mu3;
+        fo[4 * p] = sum_a / wl;
+        fo[5 * p] = sum_1 / wl;
+        fo[6 * p] = sum_2 / wl;
+        fo[7 * p] = sum_3 / wl;
+    }
+}
+
 }  // namespace
 }  // namespace mrip
 
@@ -306,8 +473,11 @@ extern "C" mrip_status mrip_tandem3_simulate(const double* d_dps, int32_t n_dp, 
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         tandem3_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
             d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, tab, out);
+    } else if (mapping == MRIP_MAP_WARP_COOP) {
+        tandem3_warp_coop_kernel<<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
+            d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, tab, out);
     } else {
-        return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD or WARP_1LANE");
+        return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");
     }
     return launch_status("mrip_tandem3_simulate");
 }
