@@ -59,6 +59,13 @@ def lib():
     L.or_forest_fire_batch.argtypes = [_c.c_int32, _c.c_int32, _f64p, _c.c_double,
                                        _c.c_int64, _i32p, _i64p, _c.c_uint64, _i32p]
     L.or_forest_fire_batch.restype = _c.c_int
+    L.or_forest_fire_skip_rep.argtypes = [_c.c_int32, _c.c_int32, _c.c_double, _c.c_double,
+                                          _c.c_double, _c.c_uint64, _c.c_uint32, _c.c_uint32,
+                                          _c.c_void_p, _i32p, _c.c_void_p, _i64p]
+    L.or_forest_fire_skip_rep.restype = _c.c_int
+    L.or_forest_fire_skip_batch.argtypes = [_c.c_int32, _c.c_int32, _f64p, _c.c_double,
+                                            _c.c_int64, _i32p, _i64p, _c.c_uint64, _i32p, _i64p]
+    L.or_forest_fire_skip_batch.restype = _c.c_int
     L.or_walk_batch.argtypes = [_f64p, _c.c_int64, _i32p, _i64p, _c.c_uint64, _c.c_int64,
                                 _i64p]
     L.or_walk_batch.restype = None
@@ -217,6 +224,42 @@ def forest_fire(L, n_steps, dps, density, dp_idx, rep_idx, seed, threads=1):
             raise MemoryError("oracle forest fire: allocation failed")
     _run_chunks(run, n, threads)
     return counts
+
+
+def forest_fire_skip_rep(L, n_steps, p_grow, p_light, density, seed, dp, rep, init_state=None):
+    """One skip-sampled forest-fire replication: (counts (T,), final (L, L),
+    near_ties)."""
+    counts = np.empty(n_steps, np.int32)
+    final = np.empty((L, L), np.uint8)
+    ties = np.zeros(1, np.int64)
+    init_ptr = None
+    if init_state is not None:
+        init_state = np.ascontiguousarray(np.asarray(init_state, dtype=np.uint8).reshape(L, L))
+        init_ptr = init_state.ctypes.data
+    rc = lib().or_forest_fire_skip_rep(int(L), int(n_steps), float(p_grow), float(p_light),
+                                       float(density), int(seed), int(dp), int(rep), init_ptr,
+                                       counts, final.ctypes.data, ties)
+    if rc != 0:
+        raise MemoryError("oracle forest fire: allocation failed")
+    return counts, final, int(ties[0])
+
+
+def forest_fire_skip(L, n_steps, dps, density, dp_idx, rep_idx, seed, threads=1):
+    """Skip-sampled forest fire per replication: (counts (n, T), near_ties (n,))."""
+    dps = np.ascontiguousarray(np.asarray(dps, dtype=np.float64).reshape(-1, 2))
+    dp_idx, rep_idx = _items(dp_idx, rep_idx)
+    n = dp_idx.size
+    counts = np.empty((n, n_steps), np.int32)
+    ties = np.zeros(n, np.int64)
+
+    def run(lo, hi):
+        rc = lib().or_forest_fire_skip_batch(int(L), int(n_steps), dps.reshape(-1), float(density),
+                                             hi - lo, dp_idx[lo:hi], rep_idx[lo:hi], int(seed),
+                                             counts[lo:hi].reshape(-1), ties[lo:hi])
+        if rc != 0:
+            raise MemoryError("oracle forest fire: allocation failed")
+    _run_chunks(run, n, threads)
+    return counts, ties
 
 
 def walk(radii, dp_idx, rep_idx, seed, max_steps=1 << 38, threads=1):

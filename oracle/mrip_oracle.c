@@ -20,7 +20,8 @@
  *   c2 = replication index, c3 = (tag << 24) | design-point index,
  *   key = (seed low 32 bits, seed high 32 bits).
  * Tags: 0 simulation, 1 lattice initial state, 2 control-mean runs,
- *       3 network initialisation, 4 minibatch order.
+ *       3 network initialisation, 4 minibatch order, 5 and 6 growth and
+ *       lightning gaps of the skip-sampled forest fire.
  *
  * Parity pins live in tests/test_oracle_*.py.  Nothing here is "parity
  * unpinned".
@@ -319,6 +320,138 @@ int or_forest_fire_batch(int32_t L, int32_t n_steps, const double *dps /* n_dp x
         int rc = or_forest_fire_rep(L, n_steps, dps[2 * d], dps[2 * d + 1], density, seed,
                                     (uint32_t)d, (uint32_t)rep_idx[i], NULL,
                                     counts + (int64_t)n_steps * i, NULL);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forest fire with skip-sampled events (an engine variant of the automaton
+ * above; same rules, same initial state from tag 1).  Instead of one word
+ * per cell, each step draws two event sets over the cells i = 0 .. L^2 - 1:
+ * growth events (each cell independently with probability p_grow) and
+ * lightning events (probability p_light).  An empty cell in the growth set
+ * becomes a tree; a tree with no burning neighbour in the lightning set
+ * ignites.  Per cell and step this is the same law as the per-cell model.
+ *
+ * Event set of probability p (Bernoulli trials over the cells in index
+ * order, sampled by the gaps between successes): with mu = -log1p(-p), gap
+ * j (j = 0, 1, ...) is K_j = floor(E_j / mu), E_j = -log(1 - u) the
+ * exponential variate of or_expo, u from words 2(j mod 2), 2(j mod 2) + 1
+ * of block (c0 = j div 2, c1 = t) under tag 5 (growth) or 6 (lightning);
+ * P(K_j >= k) = (1 - p)^k.  Events sit at pos_0 = K_0 and
+ * pos_j = pos_{j-1} + 1 + K_j while below L^2.  p = 0: no events.
+ *
+ * Where floating point decides the integer K_j, a result within a few ulps
+ * of an integer could round either way on another machine; such draws are
+ * counted in *near_ties (the tests compare only replications with none). */
+/* ------------------------------------------------------------------------ */
+static void or_skip_events(uint8_t *ev, int64_t n_cells, double p, uint32_t tag, uint64_t seed,
+                           uint32_t dp, uint32_t rep, uint32_t t, int64_t *near_ties)
+{
+    memset(ev, 0, (size_t)n_cells);
+    if (!(p > 0.0))
+        return;
+    double mu = -log1p(-p);
+    int64_t pos = -1;
+    uint32_t blk[4];
+    for (uint32_t j = 0;; ++j) {
+        if ((j & 1u) == 0)
+            or_block(seed, tag, dp, rep, t, j >> 1, blk);
+        double x = or_expo(or_u53(blk[2 * (j & 1u)], blk[2 * (j & 1u) + 1]), mu);
+        double frac = x - floor(x + 0.5);
+        if (fabs(frac) <= ldexp(x, -48) + ldexp(1.0 / mu, -50))
+            ++*near_ties;
+        /* the next event is pos + 1 + floor(x); stop once it is off the lattice */
+        if (x >= (double)(n_cells - pos - 1))
+            break;
+        pos += 1 + (int64_t)x;
+        ev[pos] = 1;
+    }
+}
+
+int or_forest_fire_skip_rep(int32_t L, int32_t n_steps, double p_grow, double p_light,
+                            double density, uint64_t seed, uint32_t dp, uint32_t rep,
+                            const uint8_t *init_state /* L*L or NULL */,
+                            int32_t *counts /* n_steps */, uint8_t *final_state /* L*L or NULL */,
+                            int64_t *near_ties)
+{
+    int64_t n_cells = (int64_t)L * L;
+    uint8_t *cur = (uint8_t *)malloc((size_t)n_cells);
+    uint8_t *nxt = (uint8_t *)malloc((size_t)n_cells);
+    uint8_t *grow = (uint8_t *)malloc((size_t)n_cells);
+    uint8_t *light = (uint8_t *)malloc((size_t)n_cells);
+    if (!cur || !nxt || !grow || !light) {
+        free(cur);
+        free(nxt);
+        free(grow);
+        free(light);
+        return -1;
+    }
+    *near_ties = 0;
+    uint32_t t_dens = or_threshold(density);
+    uint32_t blk[4];
+    if (init_state) {
+        memcpy(cur, init_state, (size_t)n_cells);
+    } else {
+        for (int64_t i = 0; i < n_cells; ++i) {
+            if (i % 4 == 0)
+                or_block(seed, 1u, dp, rep, 0u, (uint32_t)(i / 4), blk);
+            cur[i] = (blk[i % 4] < t_dens) ? 1 : 0;
+        }
+    }
+    for (int32_t t = 1; t <= n_steps; ++t) {
+        or_skip_events(grow, n_cells, p_grow, 5u, seed, dp, rep, (uint32_t)t, near_ties);
+        or_skip_events(light, n_cells, p_light, 6u, seed, dp, rep, (uint32_t)t, near_ties);
+        int32_t burning = 0;
+        for (int32_t y = 0; y < L; ++y) {
+            for (int32_t x = 0; x < L; ++x) {
+                int64_t i = (int64_t)y * L + x;
+                uint8_t s = cur[i];
+                uint8_t ns;
+                if (s == 2) {
+                    ns = 0;
+                } else if (s == 1) {
+                    int32_t up = (y + L - 1) % L, down = (y + 1) % L;
+                    int32_t left = (x + L - 1) % L, right = (x + 1) % L;
+                    int fire_near = cur[(int64_t)up * L + x] == 2 ||
+                                    cur[(int64_t)down * L + x] == 2 ||
+                                    cur[(int64_t)y * L + left] == 2 ||
+                                    cur[(int64_t)y * L + right] == 2;
+                    ns = (fire_near || light[i]) ? 2 : 1;
+                } else {
+                    ns = grow[i] ? 1 : 0;
+                }
+                nxt[i] = ns;
+                if (ns == 2)
+                    ++burning;
+            }
+        }
+        counts[t - 1] = burning;
+        uint8_t *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    if (final_state)
+        memcpy(final_state, cur, (size_t)n_cells);
+    free(cur);
+    free(nxt);
+    free(grow);
+    free(light);
+    return 0;
+}
+
+int or_forest_fire_skip_batch(int32_t L, int32_t n_steps, const double *dps /* n_dp x 2 */,
+                              double density, int64_t n_items, const int32_t *dp_idx,
+                              const int64_t *rep_idx, uint64_t seed,
+                              int32_t *counts /* n_items x n_steps */, int64_t *near_ties)
+{
+    for (int64_t i = 0; i < n_items; ++i) {
+        int32_t d = dp_idx[i];
+        int rc = or_forest_fire_skip_rep(L, n_steps, dps[2 * d], dps[2 * d + 1], density, seed,
+                                         (uint32_t)d, (uint32_t)rep_idx[i], NULL,
+                                         counts + (int64_t)n_steps * i, NULL, near_ties + i);
         if (rc != 0)
             return rc;
     }
