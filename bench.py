@@ -50,6 +50,9 @@ SM_MAX_MHZ = 2070.0
 IMUL_PER_CLK_SM = 64      # 32-bit integer multiply / multiply-add results
 DFMA_PER_CLK_SM = 2       # FP64 fused multiply-add results (1.25 TFLOP/s nominal)
 INT_MULS_PER_PHILOX = 40  # 10 rounds x 2 products x (low + high half)
+# one gap of the skip-sampled lattice: half a Philox block (20) + the
+# fixed-point log's seven 64x64-bit products, each four 32-bit products (28)
+MULS_PER_GAP = 48
 
 
 # DRAM bytes (read + write) per launch of a dominant kernel, from the ncu
@@ -146,6 +149,56 @@ class ForestFire(Workload):
         dp = (np.arange(n_items) // w["n_reps"]) % w["n_dp"]
         oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"], dp.astype(np.int32),
                            rep, self.seed, threads=threads)
+
+
+class ForestFireSkip(ForestFire):
+    """The forest-fire workload with skip-sampled events (same rules, same
+    initial state; each step draws p L^2 gaps instead of L^2 words)."""
+
+    def config(self):
+        c = super().config()
+        c["workload"] = c["workload"].replace("forest fire", "forest fire, skip-sampled events")
+        c["mapping"] = "CTA per replication, bit-packed rows, all warps draw the event gaps"
+        return c
+
+    def step(self, k_start=None, k_end=None):
+        w = self.w
+        if k_start is not None:
+            k_start.record()
+        self.eng.mrip_forest_fire_skip_simulate(self.d_dps, w["n_reps"], w["L"], w["n_steps"],
+                                                w["density"], self.seed, None, self.counts,
+                                                self.scalar)
+        if k_end is not None:
+            k_end.record()
+        self.eng.mrip_stats_reduce(self.scalar.view(w["n_dp"], w["n_reps"]), self.nmm2)
+
+    def roofline_work(self):
+        w = self.w
+        cells = float(w["L"] * w["L"])
+        p = np.asarray(w["dps"], dtype=np.float64)
+        gaps_per_step = (p[:, 0] + p[:, 1]).mean() * cells + 2.0
+        gaps = gaps_per_step * w["n_steps"] * self.units()
+        return dict(kernel="forest_fire_skip_kernel<%d>" % (w["L"] // 32), bound="alu",
+                    unit="Gop/s (32-bit integer multiply)",
+                    work=gaps * MULS_PER_GAP, peak=imul_peak_gops(),
+                    peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
+                        SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
+                    per_unit="%d int multiplies per gap (half a Philox block + the fixed-point log); "
+                             "(p_grow + p_light) L^2 + 2 gaps per step" % MULS_PER_GAP)
+
+    def make_model(self):
+        return None
+
+    def outputs(self):
+        return [self.counts, self.scalar]
+
+    def oracle_sample(self, n_items, threads):
+        import oracle
+        w = self.w
+        rep = np.arange(n_items) % w["n_reps"]
+        dp = (np.arange(n_items) // w["n_reps"]) % w["n_dp"]
+        oracle.forest_fire_skip(w["L"], w["n_steps"], w["dps"], w["density"], dp.astype(np.int32),
+                                rep, self.seed, threads=threads)
 
 
 class Walk(Workload):
@@ -502,6 +555,8 @@ def shrink(wl, n):
 def make_workload(name, rank):
     if name in ("ff128", "ff256"):
         return ForestFire(rank, "ff128" if name == "ff128" else "ff256_cv")
+    if name in ("ff128_skip", "ff256_skip"):
+        return ForestFireSkip(rank, "ff128" if name == "ff128_skip" else "ff256_cv")
     if name == "walk8":
         return Walk(rank)
     if name in ("mm1_32", "tandem"):
@@ -756,7 +811,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="ff128",
-                    choices=["ff128", "ff256", "walk8", "mm1_32", "tandem", "area_walk", "pi"])
+                    choices=["ff128", "ff256", "ff128_skip", "ff256_skip", "walk8", "mm1_32", "tandem",
+                             "area_walk", "pi"])
     ap.add_argument("--sweep", action="store_true",
                     help="area_walk: time every mapping for 1 .. 2^16 replications; "
                          "pi: time 1 .. 256 replications; tandem: mappings for 1 .. 16,384 "

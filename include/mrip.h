@@ -265,6 +265,23 @@ mrip_status mrip_forest_fire_simulate(const double *d_dps, int32_t n_dp, int64_t
                                       int32_t *d_counts, double *d_scalar, uint8_t *d_final,
                                       void *stream);
 
+/* Forest fire with skip-sampled events (an engine variant; the paper has no
+ * lattice model).  Same rules, arguments, outputs and initial state (tag 1)
+ * as mrip_forest_fire_simulate, but each step t draws its growth and
+ * lightning event sets as gaps between successes over the cells
+ * i = y L + x: gap j is K_j = floor(E_j / mu), mu = -log1p(-p), E_j the
+ * exponential variate -log(1 - u) of words 2(j mod 2), 2(j mod 2)+1 of block
+ * (c0 = j div 2, c1 = t) under tag 5 (p_grow) or tag 6 (p_light); events at
+ * K_0, K_0 + 1 + K_1, ... below L^2.  An empty cell with a growth event
+ * becomes a tree; a tree without a burning neighbour ignites on a lightning
+ * event.  Per cell and step the law is the per-cell model's with the exact
+ * probabilities; the work per step is p L^2 variates instead of L^2 words.
+ * p <= 0 (or NaN): no events; p >= 1: every cell. */
+mrip_status mrip_forest_fire_skip_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+                                           int32_t L, int32_t n_steps, double density,
+                                           uint64_t seed, const uint8_t *d_init, int32_t *d_counts,
+                                           double *d_scalar, uint8_t *d_final, void *stream);
+
 /* L1-exit walk: simple random walk on Z^2 from the origin; move m reads the
  * 2-bit field k = m mod 64 of block (0, m div 64): word k div 16, bits
  * 2(k mod 16)..+1; 0:+x 1:-x 2:+y 3:-y.  tau = moves made when |x|+|y|

@@ -360,8 +360,8 @@ static void or_skip_events(uint8_t *ev, int64_t n_cells, double p, uint32_t tag,
         if ((j & 1u) == 0)
             or_block(seed, tag, dp, rep, t, j >> 1, blk);
         double x = or_expo(or_u53(blk[2 * (j & 1u)], blk[2 * (j & 1u) + 1]), mu);
-        double frac = x - floor(x + 0.5);
-        if (fabs(frac) <= ldexp(x, -48) + ldexp(1.0 / mu, -50))
+        double nearest = floor(x + 0.5);  /* floor(x) is ambiguous only near 1, 2, ... */
+        if (nearest >= 1.0 && fabs(x - nearest) <= ldexp(x, -48) + ldexp(1.0 / mu, -50))
             ++*near_ties;
         /* the next event is pos + 1 + floor(x); stop once it is off the lattice */
         if (x >= (double)(n_cells - pos - 1))

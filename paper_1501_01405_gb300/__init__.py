@@ -107,6 +107,16 @@ def mrip_forest_fire_simulate(dps, n_reps, L, n_steps, density, seed, init=None,
         _dev(final, t.uint8, allow_none=True), _stream(stream)))
 
 
+def mrip_forest_fire_skip_simulate(dps, n_reps, L, n_steps, density, seed, init=None, counts=None,
+                                   scalar=None, final=None, stream=None):
+    t = _t()
+    _check(lib().mrip_forest_fire_skip_simulate(
+        _dev(dps, t.float64, "dps"), dps.shape[0], int(n_reps), int(L), int(n_steps),
+        float(density), int(seed), _dev(init, t.uint8, allow_none=True),
+        _dev(counts, t.int32, allow_none=True), _dev(scalar, t.float64, allow_none=True),
+        _dev(final, t.uint8, allow_none=True), _stream(stream)))
+
+
 def mrip_walk_simulate(radii, n_reps, seed, max_steps, mapping, tau, warps_per_cta=0,
                        ctas_per_sm=0, chunk=0, stream=None):
     t = _t()

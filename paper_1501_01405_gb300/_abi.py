@@ -82,6 +82,8 @@ SIGNATURES = {
                                      _P]),
     "mrip_forest_fire_simulate": (_INT, [_P, _I32, _I64, _I32, _I32, _D, _U64, _P, _P, _P, _P,
                                          _P]),
+    "mrip_forest_fire_skip_simulate": (_INT, [_P, _I32, _I64, _I32, _I32, _D, _U64, _P, _P, _P,
+                                              _P, _P]),
     "mrip_walk_simulate": (_INT, [_P, _I32, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P, _P]),
     "mrip_walk_simulate_noalloc": (_INT, [_P, _I32, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P,
                                           _P]),

@@ -76,28 +76,14 @@ constexpr int ff_threads() {
     return W == 1 ? 32 : W == 2 ? 64 : W == 4 ? 128 : W == 8 ? 256 : 512;
 }
 
+// Initial state into buffer 0 (planes T, B): from `init` (one byte per cell,
+// 0 empty, 1 tree, 2 burning) or from tag 1 (tree iff word < t_dens).
 template <int W>
-__global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
-    const double* __restrict__ dps, long long n_reps, long long rep0, int n_steps, uint32_t t_dens,
-    const __grid_constant__ RoundKeys rk, const uint8_t* __restrict__ init,
-    int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
+__device__ void ff_load_initial(uint32_t* lattice, const uint8_t* __restrict__ init, long long item,
+                                uint32_t t_dens, uint32_t rep, uint32_t dp, const RoundKeys& rk) {
     constexpr int L = 32 * W;
-    constexpr int NWORD = L * W;  // words per plane
+    constexpr int NWORD = L * W;
     constexpr int TPB = ff_threads<W>();
-    constexpr int NWARP = TPB / 32;
-    extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD]
-    __shared__ int cnt[2][64];
-    __shared__ long long red[NWARP];
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const long long item = blockIdx.x;
-    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
-    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
-    const uint32_t t_grow = threshold32(dps[2 * dp]);
-    const uint32_t t_light = threshold32(dps[2 * dp + 1]);
-    const uint32_t c3 = stream_word(0u, dp);
-
     if (init) {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(init + item * static_cast<long long>(L) * L);
         for (int k = threadIdx.x; k < NWORD; k += TPB) {
@@ -129,6 +115,70 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
             lattice[NWORD + k] = 0u;
         }
     }
+}
+
+// Planes (fin_t, fin_b) back to one byte per cell.
+template <int W>
+__device__ void ff_store_final(const uint32_t* fin_t, const uint32_t* fin_b, uint8_t* __restrict__ final_state,
+                               long long item) {
+    constexpr int L = 32 * W;
+    constexpr int NWORD = L * W;
+    constexpr int TPB = ff_threads<W>();
+    uint32_t* dst = reinterpret_cast<uint32_t*>(final_state + item * static_cast<long long>(L) * L);
+    for (int k = threadIdx.x; k < NWORD; k += TPB) {
+        const uint32_t tw = fin_t[k], bw = fin_b[k];
+        for (int r = 0; r < 8; ++r) {
+            uint32_t v = 0;
+            for (int q = 0; q < 4; ++q) {
+                const int m = 4 * r + q;
+                const uint32_t s = ((tw >> m) & 1u) ? 1u : (((bw >> m) & 1u) ? 2u : 0u);
+                v |= s << (8 * q);
+            }
+            dst[8 * k + r] = v;
+        }
+    }
+}
+
+// Per-replication scalar: the mean burning fraction (block reduction of the
+// threads' step sums).
+template <int NWARP>
+__device__ void ff_store_scalar(long long my_sum, long long* red, double* scalar, long long item, int n_steps,
+                                int L) {
+    long long s = my_sum;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < NWARP; ++w) tot += red[w];
+        scalar[item] = static_cast<double>(tot) / (static_cast<double>(n_steps) * static_cast<double>(L) * L);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
+    const double* __restrict__ dps, long long n_reps, long long rep0, int n_steps, uint32_t t_dens,
+    const __grid_constant__ RoundKeys rk, const uint8_t* __restrict__ init,
+    int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
+    constexpr int L = 32 * W;
+    constexpr int NWORD = L * W;  // words per plane
+    constexpr int TPB = ff_threads<W>();
+    constexpr int NWARP = TPB / 32;
+    extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD]
+    __shared__ int cnt[2][64];
+    __shared__ long long red[NWARP];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const long long item = blockIdx.x;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
+    const uint32_t t_grow = threshold32(dps[2 * dp]);
+    const uint32_t t_light = threshold32(dps[2 * dp + 1]);
+    const uint32_t c3 = stream_word(0u, dp);
+
+    ff_load_initial<W>(lattice, init, item, t_dens, rep, dp, rk);
     for (int i = threadIdx.x; i < 128; i += TPB) (&cnt[0][0])[i] = 0;
     __syncthreads();
 
@@ -187,35 +237,10 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
         }
     }
 
-    if (scalar) {
-        long long s = my_sum;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
-        if (lane == 0) red[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long tot = 0;
-            for (int w = 0; w < NWARP; ++w) tot += red[w];
-            scalar[item] = static_cast<double>(tot) /
-                           (static_cast<double>(n_steps) * static_cast<double>(L) * L);
-        }
-    }
+    if (scalar) ff_store_scalar<NWARP>(my_sum, red, scalar, item, n_steps, L);
     if (final_state) {
         const uint32_t* fin_t = lattice + (n_steps & 1) * 2 * NWORD;
-        const uint32_t* fin_b = fin_t + NWORD;
-        uint32_t* dst = reinterpret_cast<uint32_t*>(final_state + item * static_cast<long long>(L) * L);
-        for (int k = threadIdx.x; k < NWORD; k += TPB) {
-            const uint32_t tw = fin_t[k], bw = fin_b[k];
-            for (int r = 0; r < 8; ++r) {
-                uint32_t v = 0;
-                for (int q = 0; q < 4; ++q) {
-                    const int m = 4 * r + q;
-                    const uint32_t s = ((tw >> m) & 1u) ? 1u : (((bw >> m) & 1u) ? 2u : 0u);
-                    v |= s << (8 * q);
-                }
-                dst[8 * k + r] = v;
-            }
-        }
+        ff_store_final<W>(fin_t, fin_t + NWORD, final_state, item);
     }
 }
 
@@ -232,6 +257,283 @@ mrip_status launch_ff(const double* dps, long long n_items, long long n_reps, lo
     }
     forest_fire_kernel<W><<<static_cast<unsigned>(n_items), ff_threads<W>(), smem, st>>>(
         dps, n_reps, rep0, n_steps, t_dens, rk, init, counts, scalar, final_state);
+    return MRIP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Skip-sampled variant: the same automaton, but each step's growth and
+// lightning events are drawn as gaps between successes over the cells
+// i = 0 .. L^2 - 1 (gap j: K_j = floor(E_j / mu), mu = -log1p(-p), E_j the
+// exponential variate of words 2(j mod 2), 2(j mod 2)+1 of block
+// (c0 = j div 2, c1 = t) under tag 5 (growth) or 6 (lightning)).  Work per
+// step is p L^2 variates instead of L^2 words.
+//
+// A warp draws 64 gaps per round (lane l takes one block, i.e. two gaps), a
+// warp scan of the lanes' (2 + K_2l + K_2l+1) places the events, and each
+// event sets its bit in an event plane in shared memory (atomicOr).  All
+// warps but the last share the growth set (a round's warp totals meet in
+// shared memory), the last warp draws the lightning set (one warp draws
+// both, in turn, when the CTA has one); then all threads update the lattice
+// word-parallel:
+//   ignite = burning neighbour | lightning event,
+//   burning' = tree & ignite,
+//   tree'    = (tree & ~ignite) | (empty & growth event),
+// clearing the event words they read.  Event planes are double-buffered by
+// step parity for L <= 256, so one barrier per step (between the draw and
+// the update) suffices; L = 512 keeps one buffer and adds a second barrier.
+// ---------------------------------------------------------------------------
+// K = floor(E / mu) without the FP64 pipe: E = y57 2^-57 (the fixed-point
+// log), 2^-57 / mu = dm 2^-shift with dm a 64-bit integer (dm = the double's
+// significand scaled to [2^63, 2^64)), so K = (y57 dm) >> shift on the
+// 128-bit product, saturated at n_cells.  It differs from floor of the FP64
+// quotient only when that quotient is within a few ulps of an integer.
+struct GapScale {
+    unsigned long long dm;
+    int shift;  // >= 0; >= 128 means every gap is 0 (p >= 1)
+};
+
+__device__ __forceinline__ GapScale gap_scale(double p) {
+    GapScale g{0ull, 128};
+    if (p >= 1.0) return g;
+    const double d = 0x1p-57 / -log1p(-p);  // p in (0, 1)
+    if (!(d < 0x1p64)) {                     // mu below 2^-121: every positive E saturates
+        g.dm = ~0ull;
+        g.shift = 0;
+        return g;
+    }
+    int ex;
+    const double mant = frexp(d, &ex);  // d = mant 2^ex, mant in [0.5, 1), ex <= 64
+    g.dm = static_cast<unsigned long long>(ldexp(mant, 64));
+    g.shift = 64 - ex;  // >= 128: d < 2^-64, so y57 d < 1 and every gap is 0
+    return g;
+}
+
+__device__ __forceinline__ int gap_cells(unsigned long long y57, const GapScale& g, int n_cells) {
+    if (g.shift >= 128) return 0;
+    const unsigned long long hi = __umul64hi(y57, g.dm);
+    unsigned long long k;
+    if (g.shift >= 64) {
+        k = hi >> (g.shift - 64);
+    } else {
+        const unsigned long long lo = y57 * g.dm;
+        if (g.shift == 0)
+            k = hi ? ~0ull : lo;
+        else
+            k = (hi >> g.shift) ? ~0ull : ((hi << (64 - g.shift)) | (lo >> g.shift));
+    }
+    return k >= static_cast<unsigned long long>(n_cells) ? n_cells : static_cast<int>(k);
+}
+
+__device__ __forceinline__ unsigned long long expo_q57(uint32_t lo, uint32_t hi, const LogTable& tab) {
+    const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
+    return neg_log_q57((1ULL << 53) - (bits >> 11), tab);
+}
+
+// Call only for p > 0.
+__device__ void draw_events(uint32_t* __restrict__ ev, int n_cells, const GapScale& gs, uint32_t t, uint32_t rep,
+                            uint32_t c3, const RoundKeys& rk, const LogTable& tab) {
+    const int lane = threadIdx.x & 31;
+    int pos = -1;  // last event so far (warp-uniform)
+    for (uint32_t r = 0; pos + 1 < n_cells; ++r) {
+        const uint4 b = philox(32u * r + static_cast<uint32_t>(lane), t, rep, c3, rk);
+        const int k0 = gap_cells(expo_q57(b.x, b.y, tab), gs, n_cells);
+        const int k1 = gap_cells(expo_q57(b.z, b.w, tab), gs, n_cells);
+        const int span = 2 + k0 + k1;
+        int incl = span;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int p0 = pos + (incl - span) + 1 + k0;
+        const int p1 = p0 + 1 + k1;
+        if (p0 < n_cells) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
+        if (p1 < n_cells) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
+        pos += __shfl_sync(kFull, incl, 31);
+    }
+}
+
+// All warps draw: warps 0 .. NG-1 share the growth gaps (round r, warp w
+// takes blocks (r NG + w) 32 + lane), warp NG the lightning gaps (blocks
+// 32 r + lane) while its set is unfinished.  Each warp scans its 64 gaps; the
+// warp totals meet in shared memory (double-buffered by round parity, one
+// barrier per round) and give every warp its offset and every thread the new
+// last position, so all threads agree on when each set ends.
+template <int NWARP>
+__device__ void draw_step_events(uint32_t* __restrict__ ev_g, uint32_t* __restrict__ ev_h, int n_cells,
+                                 bool grow_on, bool light_on, const GapScale& gsg, const GapScale& gsh,
+                                 uint32_t t, uint32_t rep, uint32_t c3g, uint32_t c3h, const RoundKeys& rk,
+                                 const LogTable& tab, int (*tot)[NWARP]) {
+    static_assert(NWARP >= 2, "one-warp CTAs draw with draw_events");
+    constexpr int NG = NWARP - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int pos_g = -1, pos_h = -1;
+    for (int r = 0; grow_on || light_on; ++r) {
+        int* tt = tot[r & 1];
+        const bool mine = (warp < NG) ? grow_on : light_on;
+        int k0 = 0, k1 = 0, span = 0, incl = 0;
+        if (mine) {
+            const bool g = warp < NG;
+            const uint32_t c0 = static_cast<uint32_t>(g ? (r * NG + warp) * 32 + lane : r * 32 + lane);
+            const uint4 b = philox(c0, t, rep, g ? c3g : c3h, rk);
+            const GapScale& gs = g ? gsg : gsh;
+            k0 = gap_cells(expo_q57(b.x, b.y, tab), gs, n_cells);
+            k1 = gap_cells(expo_q57(b.z, b.w, tab), gs, n_cells);
+            span = 2 + k0 + k1;
+            incl = span;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += v;
+            }
+            if (lane == 31) tt[warp] = incl;
+        }
+        __syncthreads();
+        int before = 0, total_g = 0;
+        if (grow_on) {
+            for (int w = 0; w < NG; ++w) {
+                const int v = tt[w];
+                before += (w < warp) ? v : 0;
+                total_g += v;
+            }
+        }
+        if (mine) {
+            const bool g = warp < NG;
+            const int p0 = (g ? pos_g + before : pos_h) + (incl - span) + 1 + k0;
+            const int p1 = p0 + 1 + k1;
+            uint32_t* ev = g ? ev_g : ev_h;
+            if (p0 < n_cells) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
+            if (p1 < n_cells) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
+        }
+        if (grow_on) {
+            pos_g += total_g;
+            grow_on = pos_g + 1 < n_cells;
+        }
+        if (light_on) {
+            pos_h += tt[NG];
+            light_on = pos_h + 1 < n_cells;
+        }
+    }
+}
+
+template <int W>
+constexpr int ev_buffers() {
+    return W <= 8 ? 2 : 1;
+}
+
+template <int W>
+__global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
+    const double* __restrict__ dps, long long n_reps, long long rep0, int n_steps, uint32_t t_dens,
+    const __grid_constant__ RoundKeys rk, LogTable tab, const uint8_t* __restrict__ init,
+    int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
+    constexpr int L = 32 * W;
+    constexpr int NWORD = L * W;
+    constexpr int TPB = ff_threads<W>();
+    constexpr int NWARP = TPB / 32;
+    constexpr int NEV = ev_buffers<W>();
+    extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD], then events [NEV][G, H][NWORD]
+    uint32_t* events = lattice + 4 * NWORD;
+    __shared__ int cnt[2][64];
+    __shared__ long long red[NWARP];
+    __shared__ int tot[2][NWARP];
+
+    const int lane = threadIdx.x & 31;
+    const long long item = blockIdx.x;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
+    const double p_grow = dps[2 * dp], p_light = dps[2 * dp + 1];
+    const bool any_grow = p_grow > 0.0, any_light = p_light > 0.0;
+    const GapScale gs_grow = any_grow ? gap_scale(p_grow) : GapScale{0ull, 128};
+    const GapScale gs_light = any_light ? gap_scale(p_light) : GapScale{0ull, 128};
+    const uint32_t c3_grow = stream_word(5u, dp), c3_light = stream_word(6u, dp);
+
+    ff_load_initial<W>(lattice, init, item, t_dens, rep, dp, rk);
+    for (int k = threadIdx.x; k < NEV * 2 * NWORD; k += TPB) events[k] = 0u;
+    for (int i = threadIdx.x; i < 128; i += TPB) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+
+    long long my_sum = 0;
+    for (int t = 1; t <= n_steps; ++t) {
+        uint32_t* ev_g = events + ((NEV == 2) ? (t & 1) : 0) * 2 * NWORD;
+        uint32_t* ev_h = ev_g + NWORD;
+        if constexpr (NWARP == 1) {
+            if (any_grow) draw_events(ev_g, L * L, gs_grow, t, rep, c3_grow, rk, tab);
+            if (any_light) draw_events(ev_h, L * L, gs_light, t, rep, c3_light, rk, tab);
+        } else {
+            draw_step_events<NWARP>(ev_g, ev_h, L * L, any_grow, any_light, gs_grow, gs_light, t, rep, c3_grow,
+                                    c3_light, rk, tab, tot);
+        }
+        __syncthreads();
+        // counts of the steps before t are complete: flush a finished chunk
+        if (t > 1 && ((t - 1) & 63) == 0) {
+            const int chunk = (t - 2) >> 6;
+            for (int s = threadIdx.x; s < 64; s += TPB) {
+                const int v = cnt[chunk & 1][s];
+                cnt[chunk & 1][s] = 0;
+                my_sum += v;
+                if (counts) counts[item * n_steps + chunk * 64 + s] = v;
+            }
+        }
+        const uint32_t* cur_t = lattice + ((t - 1) & 1) * 2 * NWORD;
+        const uint32_t* cur_b = cur_t + NWORD;
+        uint32_t* nxt_t = lattice + (t & 1) * 2 * NWORD;
+        uint32_t* nxt_b = nxt_t + NWORD;
+        int c = 0;
+        for (int k = threadIdx.x; k < NWORD; k += TPB) {
+            const int y = k / W;
+            const int j = k - y * W;
+            const uint32_t tw = cur_t[k];
+            const uint32_t bw = cur_b[k];
+            const uint32_t up = cur_b[((y + L - 1) & (L - 1)) * W + j];
+            const uint32_t dn = cur_b[((y + 1) & (L - 1)) * W + j];
+            const uint32_t bwest = cur_b[y * W + ((j + W - 1) & (W - 1))];
+            const uint32_t beast = cur_b[y * W + ((j + 1) & (W - 1))];
+            const uint32_t nb = up | dn | (bw << 1) | (bwest >> 31) | (bw >> 1) | (beast << 31);
+            const uint32_t g = ev_g[k];
+            const uint32_t h = ev_h[k];
+            ev_g[k] = 0u;
+            ev_h[k] = 0u;
+            const uint32_t ignite = nb | h;
+            const uint32_t nbw = tw & ignite;
+            nxt_b[k] = nbw;
+            nxt_t[k] = (tw & ~ignite) | (~(tw | bw) & g);
+            c += __popc(nbw);
+        }
+        c = __reduce_add_sync(kFull, c);
+        if (lane == 0) atomicAdd(&cnt[((t - 1) >> 6) & 1][(t - 1) & 63], c);
+        if (NEV == 1) __syncthreads();
+    }
+    __syncthreads();
+    if (n_steps > 0) {
+        const int chunk = (n_steps - 1) >> 6;
+        const int n_slot = n_steps - chunk * 64;
+        for (int s = threadIdx.x; s < n_slot; s += TPB) {
+            const int v = cnt[chunk & 1][s];
+            my_sum += v;
+            if (counts) counts[item * n_steps + chunk * 64 + s] = v;
+        }
+    }
+    if (scalar) ff_store_scalar<NWARP>(my_sum, red, scalar, item, n_steps, L);
+    if (final_state) {
+        const uint32_t* fin_t = lattice + (n_steps & 1) * 2 * NWORD;
+        ff_store_final<W>(fin_t, fin_t + NWORD, final_state, item);
+    }
+}
+
+template <int W>
+mrip_status launch_ff_skip(const double* dps, long long n_items, long long n_reps, long long rep0, int n_steps,
+                           uint32_t t_dens, const RoundKeys& rk, const LogTable& tab, const uint8_t* init,
+                           int32_t* counts, double* scalar, uint8_t* final_state, cudaStream_t st) {
+    const size_t nword = static_cast<size_t>(32 * W) * W;
+    const size_t smem = (4 + 2 * ev_buffers<W>()) * nword * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(forest_fire_skip_kernel<W>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return cuda_status(e, "forest fire (skip): shared memory attribute");
+    }
+    forest_fire_skip_kernel<W><<<static_cast<unsigned>(n_items), ff_threads<W>(), smem, st>>>(
+        dps, n_reps, rep0, n_steps, t_dens, rk, tab, init, counts, scalar, final_state);
     return MRIP_OK;
 }
 
@@ -273,6 +575,43 @@ mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, 
     return launch_status("mrip_forest_fire_simulate");
 }
 }  // namespace mrip
+
+extern "C" mrip_status mrip_forest_fire_skip_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+                                                      int32_t L, int32_t n_steps, double density,
+                                                      uint64_t seed, const uint8_t* d_init,
+                                                      int32_t* d_counts, double* d_scalar,
+                                                      uint8_t* d_final, void* stream) {
+    if (n_dp < 0 || n_reps < 0 || n_steps < 0)
+        return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: negative size");
+    if (L < 32 || L > 512 || L % 32 != 0 || (L & (L - 1)) != 0)
+        return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: L must be 32, 64, 128, 256 or 512");
+    if (!(density >= 0.0 && density < 1.0))
+        return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: density must be in [0, 1)");
+    if (n_dp >= (1 << 24) || n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: n_dp < 2^24 and replication indices < 2^32");
+    const long long n_items = static_cast<long long>(n_dp) * n_reps;
+    if (n_items == 0) return MRIP_OK;
+    if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: too many replications");
+    if (!d_dps) return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: null design points");
+    if ((d_init && (reinterpret_cast<uintptr_t>(d_init) & 15u)) ||
+        (d_final && (reinterpret_cast<uintptr_t>(d_final) & 15u)))
+        return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: state buffers need 16-byte alignment");
+    LogTable tab;
+    mrip_status rc = log_table(&tab);
+    if (rc != MRIP_OK) return rc;
+    const RoundKeys rk = expand_key(seed);
+    const uint32_t t_dens = threshold32(density);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (L) {
+        case 32: rc = launch_ff_skip<1>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 64: rc = launch_ff_skip<2>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 128: rc = launch_ff_skip<4>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 256: rc = launch_ff_skip<8>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 512: rc = launch_ff_skip<16>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+    }
+    if (rc != MRIP_OK) return rc;
+    return launch_status("mrip_forest_fire_skip_simulate");
+}
 
 extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
                                                  int32_t L, int32_t n_steps, double density,

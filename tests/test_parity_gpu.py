@@ -455,3 +455,79 @@ def test_pi_bit_exact(eng, torch_mod, n_draws):
     eng.mrip_pi_simulate(reps, n_draws, 42, hits)
     ref = oracle.pi_hits(np.arange(reps), n_draws, 42, threads=threads())
     assert np.array_equal(hits.cpu().numpy(), ref)
+
+
+# ------------------------------------------------------------------ skip-sampled forest fire
+def _skip_run(eng, t, dps, n_reps, L, n_steps, density, seed, init=None):
+    items = len(dps) * n_reps
+    counts = t.empty(max(1, items * n_steps), dtype=t.int32, device="cuda")
+    scalar = t.empty(items, dtype=t.float64, device="cuda")
+    final = t.empty(items * L * L, dtype=t.uint8, device="cuda")
+    eng.mrip_forest_fire_skip_simulate(dev(t, dps), n_reps, L, n_steps, density, seed,
+                                       None if init is None else dev(t, init), counts, scalar, final)
+    return (counts.cpu().numpy()[:items * n_steps].reshape(items, n_steps), scalar.cpu().numpy(),
+            final.cpu().numpy().reshape(items, L, L))
+
+
+@pytest.mark.parametrize("L", [32, 64, 128, 256, 512])
+@pytest.mark.parametrize("n_steps", [1, 64, 130])
+def test_forest_fire_skip_bit_exact(eng, torch_mod, L, n_steps):
+    """Event sets of tiny, moderate and large probabilities (several 64-gap
+    rounds per step), over a ragged number of steps and every lattice size."""
+    t = torch_mod
+    if L == 512 and n_steps == 130:
+        n_steps = 20
+    dps = np.array([[0.01, 1e-5], [0.3, 0.05], [0.97, 0.0]])
+    n_reps = 2
+    gc, gsc, gs = _skip_run(eng, t, dps, n_reps, L, n_steps, 0.5, 42)
+    compared = 0
+    for i, (d, r) in enumerate(zip(*oracle.all_items(len(dps), n_reps))):
+        rc, rs, ties = oracle.forest_fire_skip_rep(L, n_steps, dps[d, 0], dps[d, 1], 0.5, 42, d, r)
+        if ties:
+            continue
+        compared += 1
+        assert np.array_equal(gc[i], rc), (d, r)
+        assert np.array_equal(gs[i], rs), (d, r)
+        assert gsc[i] == rc.sum() / (n_steps * L * L)
+    assert compared == len(dps) * n_reps
+
+
+def test_forest_fire_skip_edges(eng, torch_mod):
+    """No events (p = 0), every cell (p = 1), zero steps, given states."""
+    t = torch_mod
+    L, n_steps, n_reps = 64, 70, 3
+    rng = np.random.default_rng(9)
+    init = rng.integers(0, 3, size=(2 * n_reps, L, L)).astype(np.uint8)
+    init[0] = 1
+    init[0, 10, 10] = 2
+    dps = np.array([[0.0, 0.0], [1.0, 0.5]])
+    gc, _, gs = _skip_run(eng, t, dps, n_reps, L, n_steps, 0.5, 7, init=init)
+    for i, (d, r) in enumerate(zip(*oracle.all_items(2, n_reps))):
+        rc, rs, ties = oracle.forest_fire_skip_rep(L, n_steps, dps[d, 0], dps[d, 1], 0.5, 7, d, r,
+                                                   init_state=init[i])
+        assert ties == 0
+        assert np.array_equal(gc[i], rc) and np.array_equal(gs[i], rs)
+    assert gc[0, :31].tolist() == [4 * k for k in range(1, 32)]
+    _, _, gs0 = _skip_run(eng, t, np.array([[0.01, 1e-5]]), 2, 128, 0, 0.37, 42)
+    for r in range(2):
+        _, rs, _ = oracle.forest_fire_skip_rep(128, 0, 0.01, 1e-5, 0.37, 42, 0, r)
+        assert np.array_equal(gs0[r], rs)
+
+
+def test_forest_fire_skip_workload_full_sampled(eng, torch_mod):
+    """The 128x128, 1,000-step, 1,024-replication workload with skip-sampled
+    events; four replications bit-exact against the oracle."""
+    t = torch_mod
+    w = mrip_inputs.workload("ff128")
+    counts = t.empty(w["n_reps"] * w["n_steps"], dtype=t.int32, device="cuda")
+    eng.mrip_forest_fire_skip_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], w["n_steps"],
+                                       w["density"], w["seed"], None, counts)
+    gc = counts.cpu().numpy().reshape(w["n_reps"], w["n_steps"])
+    pick = np.array([0, 1, 511, 1023])
+    rc, ties = oracle.forest_fire_skip(w["L"], w["n_steps"], w["dps"], w["density"],
+                                       np.zeros(4, np.int32), pick, w["seed"], threads=threads())
+    for k in range(4):
+        if ties[k] == 0:
+            assert np.array_equal(gc[pick[k]], rc[k])
+    assert np.count_nonzero(ties == 0) >= 3
+    assert gc.min() >= 0 and gc.max() <= w["L"] ** 2
