@@ -83,21 +83,27 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
 // (Tang's table-driven reduction, ACM TOMS 16(4), 1990, carried out in
 // integers).  With 1 - u = K 2^-53, K in [1, 2^53], K = 2^e M, M in [1, 2):
 //   -log(1 - u) = (53 - e) ln 2 - ln M,
-//   ln M = ln c_j + log1p(r),  r = M / c_j - 1,  |r| < 2^-9,
-// c_j the centre of the j-th of 256 slices of [1, 2) (j = the 8 bits after
+//   ln M = ln c_j + log1p(r),  r = M / c_j - 1,  |r| < 2^-13,
+// c_j the centre of the j-th of 4096 slices of [1, 2) (j = the 12 bits after
 // the leading one), 1/c_j stored as a 63-bit fraction, ln c_j as a 64-bit
-// fraction, and log1p(r) = r + r^2 (-1/2 + r/3 - r^2/4 + r^3/5 - r^4/6)
-// (truncation below 2^-64), r in signed Q.64 and the bracket in Q.63.  The result carries an absolute
-// error below 2^-56 before its one rounding to double, i.e. within about an
-// ulp for -log(1 - u) > 1/16 and far below the ulp of any sum it enters.
+// fraction.  log1p(r) = r - r^2/2 + r^2 (r/3 - r^2/4) (the r^5 term is below
+// 2^-67): r and r^2 in 64-bit fixed point, the bracket and its product with
+// r^2 in 32-bit pieces (one wide multiply), since their weight is below
+// 2^-40.  The result carries an absolute error below 2^-56 (2^-56.96 in an
+// exhaustive check of slice edges and centres at every exponent) before its
+// one rounding to double, i.e. within about an ulp for -log(1 - u) > 1/16
+// and far below the ulp of any sum it enters.
 // ---------------------------------------------------------------------------
+constexpr int kLogSliceBits = 12;
+constexpr int kLogSlices = 1 << kLogSliceBits;
+
 struct __align__(16) LogSlice {
     unsigned long long inv;  // round(2^63 / c_j)
     unsigned long long lnc;  // round(-ln(inv 2^-63) 2^64) = ln c_j to 2^-64
 };
 
 struct LogTable {
-    const LogSlice* slice;       // 256 entries, device memory
+    const LogSlice* slice;       // kLogSlices entries, device memory
     unsigned long long ln2_q64;  // round(ln 2 * 2^64)
 };
 
@@ -109,28 +115,27 @@ mrip_status log_table(LogTable* out);
 // so it fits a signed 64-bit word).
 __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, const LogTable& tab) {
     const int lz = __clzll(K);
-    const unsigned long long m = K << lz;  // bit 63 set: M = m 2^-63
+    const unsigned long long m = K << lz;                   // bit 63 set: M = m 2^-63
     const unsigned long long n = static_cast<unsigned long long>(lz - 10);  // 53 - e
-    const int j = static_cast<int>((m >> 55) & 0xFFu);
+    const int j = static_cast<int>((m >> (63 - kLogSliceBits)) & (kLogSlices - 1));
     const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tab.slice) + j);
-    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62
+    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62, |r 2^64| < 2^51
     const unsigned long long hi = __umul64hi(m, e.x);
     const unsigned long long lo = m * e.x;
     const long long R = static_cast<long long>(((hi - (1ULL << 62)) << 2) | (lo >> 62));
-    // Q(r) = -1/2 + r/3 - r^2/4 + r^3/5 - r^4/6 in Q.63 (|Q| < 0.51)
-    long long q = -1537228672809129301LL;              // -2^63 / 6
-    q = 1844674407370955162LL + __mul64hi(R, q);       //  2^63 / 5
-    q = -2305843009213693952LL + __mul64hi(R, q);      // -2^63 / 4
-    q = 3074457345618258603LL + __mul64hi(R, q);       //  2^63 / 3
-    q = -4611686018427387904LL + __mul64hi(R, q);      // -2^63 / 2
-    const long long r2 = __mul64hi(R, R);              // r^2 2^64
-    const long long l1p = R + 2 * __mul64hi(r2, q);   // log1p(r) 2^64
-    // y 2^57 = n ln2 2^57 - lnc 2^57 - log1p 2^57
+    const long long r2 = __mul64hi(R, R);                               // r^2 2^64 < 2^38
+    const int a = static_cast<int>(R >> 20);                            // r 2^44
+    const int q = __mulhi(a, 1431655766) - static_cast<int>(r2 >> 22);  // (r/3 - r^2/4) 2^44
+    const long long tail = (static_cast<long long>(static_cast<int>(r2 >> 7)) * q) >> 37;  // r^2 q 2^64
+    const long long l1p = R - (r2 >> 1) + tail;                          // log1p(r) 2^64
+    const long long s63 = static_cast<long long>(e.y >> 1) + (l1p >> 1);  // ln M 2^63
+    // n ln2 2^57, rounded (n <= 53, so the product stays below 2^70)
     const unsigned long long p_lo = n * tab.ln2_q64;
     const unsigned long long p_hi = __umul64hi(n, tab.ln2_q64);
-    const unsigned long long nln2 = (p_hi << 57) | (p_lo >> 7);
-    // near y = 0 (K close to 2^53) the truncations may undershoot: clamp
-    const long long y = static_cast<long long>(nln2 - (e.y >> 7) - static_cast<unsigned long long>(l1p >> 7));
+    const unsigned long long r_lo = p_lo + 64u;
+    const unsigned long long nln2 = ((p_hi + (r_lo < p_lo ? 1u : 0u)) << 57) | (r_lo >> 7);
+    // near y = 0 (K close to 2^53) the roundings may undershoot: clamp
+    const long long y = static_cast<long long>(nln2) - ((s63 + 32) >> 6);
     return y > 0 ? static_cast<unsigned long long>(y) : 0ULL;
 }
 

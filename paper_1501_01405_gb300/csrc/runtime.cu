@@ -79,12 +79,12 @@ int* device_error_flags() {
 }
 
 namespace {
-// 1/c_j and ln c_j for the 256 slices of [1, 2), from the host's long-double
+// 1/c_j and ln c_j for the slices of [1, 2), from the host's long-double
 // logarithm (64-bit or wider mantissa).
 void build_log_slices(std::vector<LogSlice>& t) {
-    t.resize(256);
-    for (int j = 0; j < 256; ++j) {
-        const long double c = 1.0L + (static_cast<long double>(j) + 0.5L) / 256.0L;
+    t.resize(kLogSlices);
+    for (int j = 0; j < kLogSlices; ++j) {
+        const long double c = 1.0L + (static_cast<long double>(j) + 0.5L) / static_cast<long double>(kLogSlices);
         const unsigned long long inv =
             static_cast<unsigned long long>(ldexpl(1.0L / c, 63) + 0.5L);
         const long double ic = ldexpl(static_cast<long double>(inv), -63);
