@@ -163,6 +163,67 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
 }
 
 // ---------------------------------------------------------------------------
+// Times in 64-bit fixed point.  GB300 retires about two FP64 operations per
+// SM-clock and over forty 32-bit integer multiplies, so the queue recurrences
+// (additions, subtractions and maxima only) run on integers: a time t is held
+// as round(t 2^48).  A variate is E / rate with E = y57 2^-57 from the
+// fixed-point log, i.e. round(y57 * (2^-9 / rate)), the factor stored as a
+// 64-bit significand cm and a shift cs (2^-9 / rate = cm 2^-cs).  Variates
+// then carry an error of half a unit (2^-49), unbiased, instead of half an
+// ulp of a double, and every recurrence step is exact; the outputs agree with
+// FP64 evaluation far inside 1e-12 as long as the variates are not tiny
+// against 2^-48: rates are limited to [2^-6, 2^4] (mean variate >= 1/16).
+// A variate is then below 36.8 * 64 < 2^11.3 time units (E <= 53 ln 2);
+// while the largest state stays below 2^12 (2^60 units) one more step stays
+// below 2^61.5, so nothing overflows.  Design points with other rates run the
+// FP64 recurrence, and a replication whose sojourn time reaches 2^12
+// restarts in FP64.  Means of single variates (the early-window features)
+// are summed in FP64 from the same log values, where a variate's relative
+// precision matters.
+// ---------------------------------------------------------------------------
+constexpr int kFixBits = 48;
+constexpr long long kFixGuard = 1LL << 60;
+constexpr long long kFixNegInf = -(1LL << 62);  // "empty" state: v - A stays above -2^63
+
+struct FixScale {
+    unsigned long long cm;  // in [2^63, 2^64)
+    int cs;                 // in [64, 127]
+};
+
+__device__ __forceinline__ bool fix_rate_ok(double rate) { return rate >= 0x1p-6 && rate <= 0x1p4; }
+
+__device__ __forceinline__ FixScale fix_scale(double rate) {
+    int ex;
+    const double mant = frexp(0x1p-9 / rate, &ex);  // ex in [-12, -2] for the rates above
+    return FixScale{static_cast<unsigned long long>(ldexp(mant, 64)), 64 - ex};
+}
+
+// round(y57 cm 2^-cs)
+__device__ __forceinline__ long long to_fix(unsigned long long y57, const FixScale& f) {
+    const unsigned long long hi = __umul64hi(y57, f.cm);
+    if (f.cs == 64) return static_cast<long long>(hi + ((y57 * f.cm) >> 63));
+    const int sh = f.cs - 64;
+    return static_cast<long long>((hi + (1ULL << (sh - 1))) >> sh);
+}
+
+struct U128 {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(long long v) {  // v >= 0
+        const unsigned long long u = static_cast<unsigned long long>(v);
+        lo += u;
+        hi += (lo < u) ? 1u : 0u;
+    }
+    __device__ __forceinline__ double to_double() const {  // value 2^-48
+        return static_cast<double>(hi) * 0x1p16 + static_cast<double>(lo) * 0x1p-48;
+    }
+};
+
+__device__ __forceinline__ unsigned long long word_k(uint32_t lo, uint32_t hi) {
+    const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
+    return (1ULL << 53) - (bits >> 11);
+}
+
+// ---------------------------------------------------------------------------
 // Tandem: V_{n,j} = max(V_{n-1,j} - A_n, V_{n,j-1}) + S_{n,j}
 // ---------------------------------------------------------------------------
 struct TandemOut {
@@ -193,9 +254,51 @@ __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long 
                  i_mu3 = 0x1p-57 / mu3;
     const uint32_t c3 = stream_word(tag, dp);
     const long long w_len = (n_clients < window) ? n_clients : window;
-    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
     double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
-    for (long long n = 0; n < n_clients; ++n) {
+    bool fixed_done = false;
+    if (fix_rate_ok(lam) && fix_rate_ok(mu1) && fix_rate_ok(mu2) && fix_rate_ok(mu3)) {
+        const FixScale fl = fix_scale(lam), f1 = fix_scale(mu1), f2 = fix_scale(mu2), f3 = fix_scale(mu3);
+        long long v1 = kFixNegInf, v2 = kFixNegInf, v3 = kFixNegInf;
+        U128 sy;
+        double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        bool overflow = false;
+        for (long long n = 0; n < n_clients; ++n) {
+            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            const unsigned long long ya = neg_log_q57(word_k(b0.x, b0.y), tab);
+            const unsigned long long y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
+            const unsigned long long y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
+            const unsigned long long y3 = neg_log_q57(word_k(b1.z, b1.w), tab);
+            const long long a = to_fix(ya, fl);
+            long long q = v1 - a;
+            v1 = ((q > 0) ? q : 0) + to_fix(y1, f1);
+            q = v2 - a;
+            v2 = ((q > v1) ? q : v1) + to_fix(y2, f2);
+            q = v3 - a;
+            v3 = ((q > v2) ? q : v2) + to_fix(y3, f3);
+            sy.add(v3);
+            if (n < w_len) {  // the same variates as doubles (expo_fast)
+                wa += __ull2double_rn(ya) * i_lam;
+                w1 += __ull2double_rn(y1) * i_mu1;
+                w2 += __ull2double_rn(y2) * i_mu2;
+                w3 += __ull2double_rn(y3) * i_mu3;
+            }
+            if (v3 >= kFixGuard) {
+                overflow = true;
+                break;
+            }
+        }
+        if (!overflow) {
+            fixed_done = true;
+            sum_y = sy.to_double();
+            sum_a = wa;
+            sum_1 = w1;
+            sum_2 = w2;
+            sum_3 = w3;
+        }
+    }
+    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
+    for (long long n = 0; !fixed_done && n < n_clients; ++n) {
         const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
         const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
         const double a = expo_fast(b0.x, b0.y, tab, i_lam);

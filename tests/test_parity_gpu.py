@@ -132,6 +132,29 @@ def test_tandem_thread_and_wlp(eng, torch_mod):
         np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, ref_f, rtol=REL)
 
 
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE"])
+def test_tandem_fixed_point_fallbacks(eng, torch_mod, mapping):
+    """Times run in 48-bit fixed point; a slow rate (below 2^-6) sends a design
+    point to FP64 and an unstable queue whose sojourn time passes 2^12
+    restarts its replication in FP64.  All within 1e-12 of the oracle."""
+    t = torch_mod
+    dps = np.array([[0.9, 1.0, 1.1, 1.2],      # fixed point all the way
+                    [0.005, 0.01, 0.02, 0.03],  # rates below 2^-6: FP64
+                    [2.0, 1.0, 1.5, 1.5],       # unstable: passes 2^12 after ~8,000 clients
+                    [0.5, 16.0, 1.0, 3.0],      # a service rate at the upper bound 2^4
+                    [0.5, 2.0**30, 1.0, 3.0]])  # above it: FP64
+    n_reps, n_clients, window = 3, 12000, 50
+    ry, rf = oracle.tandem3(dps, *oracle.all_items(5, n_reps), n_clients, 42, window=window,
+                            threads=threads())
+    y = t.empty(5 * n_reps, dtype=t.float64, device="cuda")
+    f = t.empty(8 * 5 * n_reps, dtype=t.float64, device="cuda")
+    eng.mrip_tandem3_simulate(dev(t, dps), 0, n_reps, n_clients, window, 42, 0,
+                              getattr(eng, "MRIP_MAP_" + mapping), y, f)
+    np.testing.assert_allclose(y.cpu().numpy(), ry, rtol=REL)
+    np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
+    assert ry[6:9].min() > 4096 / 4  # the unstable point really grows
+
+
 def test_tandem_offset_tag_and_short_runs(eng, torch_mod):
     t = torch_mod
     dps = mrip_inputs.tandem_design_points(3, seed=4)
