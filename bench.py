@@ -53,6 +53,10 @@ INT_MULS_PER_PHILOX = 40  # 10 rounds x 2 products x (low + high half)
 # one gap of the skip-sampled lattice: half a Philox block (20) + the
 # fixed-point log's seven 64x64-bit products, each four 32-bit products (28)
 MULS_PER_GAP = 48
+# one exponential variate in 48-bit fixed point: the log's products (26: the
+# 64x64-bit m * 1/c and r^2, the 32-bit tail, n ln 2) + the 64x64-bit scaling
+# by 2^-9 / rate (8)
+MULS_PER_FIXED_VARIATE = 34
 
 
 # DRAM bytes (read + write) per launch of a dominant kernel, from the ncu
@@ -280,7 +284,9 @@ class Queue(Workload):
         if self.key == "mm1_32":
             return {"workload": "mm1_32: M/M/1 Lindley, lambda 0.9, mu 1, 1000 clients, 32 "
                                 "replications", "n_reps": w["n_reps"], "n_clients": w["n_clients"],
-                    "seed": self.seed, "mapping": "warp-cooperative max-plus scan"}
+                    "seed": self.seed, "mapping": "CTA per replication, block scan of max-plus "
+                                                  "maps, 48-bit fixed-point times",
+                    "launch": "each step (simulate + statistics) replayed as one CUDA graph"}
         return {"workload": "tandem: 3-station tandem, %d design points x %d replications x %d "
                             "clients (plain estimator)" % (w["n_dp"], w["n_reps"], w["n_clients"]),
                 "n_dp": w["n_dp"], "n_reps": w["n_reps"], "n_clients": w["n_clients"],
@@ -302,7 +308,7 @@ class Queue(Workload):
             k_start.record()
         if self.key == "mm1_32":
             self.eng.mrip_mm1_simulate(self.d_dps, w["n_reps"], w["n_clients"], self.seed,
-                                       self.eng.MRIP_MAP_WARP_COOP, self.y)
+                                       self.eng.MRIP_MAP_CTA, self.y)
         else:
             self.eng.mrip_tandem3_simulate(self.d_dps, 0, w["n_reps"], w["n_clients"],
                                            w["window"], self.seed, 0, self.eng.MRIP_MAP_THREAD,
@@ -313,21 +319,31 @@ class Queue(Workload):
 
     launches_per_step = 2
 
+    @property
+    def graph_step(self):
+        return self.key == "mm1_32"
+
     def roofline_work(self):
         w = self.w
         clients = self.units() * w["n_clients"]
+        blocks = 1 if self.key == "mm1_32" else 2
         logs = 2 if self.key == "mm1_32" else 4
-        return dict(kernel="mm1_warp_coop_kernel" if self.key == "mm1_32"
+        per_client = blocks * INT_MULS_PER_PHILOX + logs * MULS_PER_FIXED_VARIATE
+        return dict(kernel="mm1_cta_kernel (graph with the statistics kernel)" if self.key == "mm1_32"
                     else "tandem3_serial_kernel", bound="alu",
-                    unit="G exponential variates/s", work=clients * logs,
-                    peak=None, peak_source="see DESIGN.md (FP64-pipe bound)",
-                    per_unit="%d exponential variates per client" % logs)
+                    unit="Gop/s (32-bit integer multiply)", work=clients * per_client,
+                    peak=imul_peak_gops(),
+                    peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
+                        SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
+                    per_unit="%d int multiplies per client: %d Philox block(s) (40 each) + %d "
+                             "fixed-point variates (%d each: log 26, scaling 8)" % (
+                                 per_client, blocks, logs, MULS_PER_FIXED_VARIATE))
 
     def make_model(self):
         w = self.w
         if self.key == "mm1_32":
             m = self.eng.Model(self.eng.MRIP_MM1, n_clients=w["n_clients"])
-            m.set_plan('{"mapping": 3}')
+            m.set_plan('{"mapping": %d}' % self.eng.MRIP_MAP_CTA)
             return m
         return self.eng.Model(self.eng.MRIP_TANDEM3, n_clients=w["n_clients"],
                               window=w["window"])
@@ -866,6 +882,24 @@ def main():
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()
+    if getattr(wl, "graph_step", False):
+        # latency-bound steps: replay the step's launches as one CUDA graph, so
+        # the device time is not the host's launch rate
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            wl.step()
+        torch.cuda.synchronize()
+
+        def graph_step_fn(k_start=None, k_end=None):
+            if k_start is not None:
+                k_start.record()
+            graph.replay()
+            if k_end is not None:
+                k_end.record()
+        wl.step = graph_step_fn
+        for _ in range(args.warmup):
+            wl.step()
+        torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]

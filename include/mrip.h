@@ -226,7 +226,9 @@ mrip_status mrip_expo(const uint32_t *d_lo, const uint32_t *d_hi, const double *
  * W_{n+1} = max(0, W_n + S_n - A_{n+1}).  Outputs (device, n_dp * n_reps,
  * any may be NULL): mean wait W, mean idle max(0, A_{n+1} - W_n - S_n),
  * mean time in system W + S over n < n_clients.  mapping: THREAD,
- * WARP_1LANE or WARP_COOP (AUTO = THREAD). */
+ * WARP_1LANE, WARP_COOP or CTA (one replication per CTA of up to 1,024
+ * threads, ~4 clients each, block scan of the maps; for a few replications
+ * whose latency matters).  AUTO = THREAD. */
 mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
                               int64_t n_clients, uint64_t seed, int mapping,
                               double *d_wait, double *d_idle, double *d_system, void *stream);

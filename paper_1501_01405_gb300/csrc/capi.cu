@@ -288,7 +288,7 @@ bool mapping_allowed(int kind, int mapping) {
     switch (kind) {
         case MRIP_MM1:
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD ||
-                   mapping == MRIP_MAP_WARP_1LANE || mapping == MRIP_MAP_WARP_COOP;
+                   mapping == MRIP_MAP_WARP_1LANE || mapping == MRIP_MAP_WARP_COOP || mapping == MRIP_MAP_CTA;
         case MRIP_TANDEM3:
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE ||
                    mapping == MRIP_MAP_WARP_COOP;
@@ -313,6 +313,7 @@ std::vector<Plan> candidates(int kind) {
     switch (kind) {
         case MRIP_MM1:
             add(MRIP_MAP_THREAD, 0, 0, 0);
+            add(MRIP_MAP_CTA, 0, 0, 0);
             add(MRIP_MAP_WARP_COOP, 0, 0, 0);
             add(MRIP_MAP_WARP_1LANE, 0, 0, 0);
             break;

@@ -168,9 +168,10 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
 // (additions, subtractions and maxima only) run on integers: a time t is held
 // as round(t 2^48).  A variate is E / rate with E = y57 2^-57 from the
 // fixed-point log, i.e. round(y57 * (2^-9 / rate)), the factor stored as a
-// 64-bit significand cm and a shift cs (2^-9 / rate = cm 2^-cs).  Variates
-// then carry an error of half a unit (2^-49), unbiased, instead of half an
-// ulp of a double, and every recurrence step is exact; the outputs agree with
+// 64-bit multiplier cm = round(2^57 / rate) (2^-9 / rate = cm 2^-66).  A
+// variate then carries the multiplier's relative error (2^-53, as an FP64
+// division would) plus half a unit (2^-49), and every recurrence step is
+// exact, where FP64 rounds each addition; the outputs agree with
 // FP64 evaluation far inside 1e-12 as long as the variates are not tiny
 // against 2^-48: rates are limited to [2^-6, 2^4] (mean variate >= 1/16).
 // A variate is then below 36.8 * 64 < 2^11.3 time units (E <= 53 ln 2);
@@ -185,25 +186,16 @@ constexpr int kFixBits = 48;
 constexpr long long kFixGuard = 1LL << 60;
 constexpr long long kFixNegInf = -(1LL << 62);  // "empty" state: v - A stays above -2^63
 
-struct FixScale {
-    unsigned long long cm;  // in [2^63, 2^64)
-    int cs;                 // in [64, 127]
-};
-
+// 2^-9 / rate as cm 2^-66 (cm in [2^53, 2^63] for the rates above: at least
+// 53 significant bits), so that round(y57 2^-9 / rate) = (hi(y57 cm) + 2) >> 2.
 __device__ __forceinline__ bool fix_rate_ok(double rate) { return rate >= 0x1p-6 && rate <= 0x1p4; }
 
-__device__ __forceinline__ FixScale fix_scale(double rate) {
-    int ex;
-    const double mant = frexp(0x1p-9 / rate, &ex);  // ex in [-12, -2] for the rates above
-    return FixScale{static_cast<unsigned long long>(ldexp(mant, 64)), 64 - ex};
+__device__ __forceinline__ unsigned long long fix_scale(double rate) {
+    return static_cast<unsigned long long>(0x1p57 / rate + 0.5);
 }
 
-// round(y57 cm 2^-cs)
-__device__ __forceinline__ long long to_fix(unsigned long long y57, const FixScale& f) {
-    const unsigned long long hi = __umul64hi(y57, f.cm);
-    if (f.cs == 64) return static_cast<long long>(hi + ((y57 * f.cm) >> 63));
-    const int sh = f.cs - 64;
-    return static_cast<long long>((hi + (1ULL << (sh - 1))) >> sh);
+__device__ __forceinline__ long long to_fix(unsigned long long y57, unsigned long long cm) {
+    return static_cast<long long>((__umul64hi(y57, cm) + 2u) >> 2);
 }
 
 struct U128 {
@@ -233,7 +225,7 @@ struct TandemOut {
 };
 
 template <bool kLane0Only>
-__global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long n_items,
+__global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __restrict__ dps, long long n_items,
                                       long long n_reps, long long rep0, long long n_clients,
                                       long long window, uint32_t tag,
                                       const __grid_constant__ RoundKeys rk, LogTable tab,
@@ -257,7 +249,8 @@ __global__ void tandem3_serial_kernel(const double* __restrict__ dps, long long 
     double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
     bool fixed_done = false;
     if (fix_rate_ok(lam) && fix_rate_ok(mu1) && fix_rate_ok(mu2) && fix_rate_ok(mu3)) {
-        const FixScale fl = fix_scale(lam), f1 = fix_scale(mu1), f2 = fix_scale(mu2), f3 = fix_scale(mu3);
+        const unsigned long long fl = fix_scale(lam), f1 = fix_scale(mu1), f2 = fix_scale(mu2),
+                                 f3 = fix_scale(mu3);
         long long v1 = kFixNegInf, v2 = kFixNegInf, v3 = kFixNegInf;
         U128 sy;
         double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
@@ -501,6 +494,208 @@ __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// M/M/1, one replication per CTA (few replications of a latency-bound
+// length): thread i takes the contiguous clients [i k, (i+1) k).  Pass 1
+// composes each thread's Lindley maps W -> max(c, W + d); a block scan (warp
+// shuffles, then the warp totals in shared memory) gives every thread the
+// map of all clients before it, whose value at W_0 = 0 is its entry wait;
+// pass 2 replays the thread's clients with the plain recurrence.  Times run
+// in the 48-bit fixed point of the tandem, so composition is exact and the
+// sums are exact integers (order-free); c and d saturate at +-2^61, which
+// changes no map value for waits in [0, 2^60] unless a wait passes 2^60 --
+// then, or for rates outside [2^-6, 2^4], the CTA redoes the replication in
+// FP64 with the same structure (maps with -inf, sums in a fixed tree).
+// ---------------------------------------------------------------------------
+constexpr long long kSat = 1LL << 61;
+
+__device__ __forceinline__ long long sat61(long long x) { return x > kSat ? kSat : (x < -kSat ? -kSat : x); }
+
+struct FixMap {
+    long long c, d;
+};
+__device__ __forceinline__ FixMap fcompose(const FixMap& f, const FixMap& g) {  // g after f
+    const long long cc = sat61(f.c + g.d);
+    return FixMap{g.c > cc ? g.c : cc, sat61(f.d + g.d)};
+}
+struct DblMap {
+    double c, d;
+};
+__device__ __forceinline__ DblMap dcompose(const DblMap& f, const DblMap& g) {
+    const double cc = f.c + g.d;
+    return DblMap{g.c > cc ? g.c : cc, f.d + g.d};
+}
+
+template <class Map>
+__device__ __forceinline__ Map shfl_up_map(const Map& m, int off) {
+    return Map{__shfl_up_sync(kFull, m.c, off), __shfl_up_sync(kFull, m.d, off)};
+}
+
+// Exclusive block scan of per-thread maps (thread order); `identity` for
+// thread 0.  smem: one Map per warp.
+template <class Map, class Compose>
+__device__ Map block_exclusive_map(Map f, Map identity, Map* smem, Compose compose) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    Map incl = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Map prev = shfl_up_map(incl, off);
+        if (lane >= off) incl = compose(prev, incl);
+    }
+    if (lane == 31) smem[warp] = incl;
+    __syncthreads();
+    Map before = identity;  // maps of the earlier warps, composed in order
+    for (int w = 0; w < warp; ++w) before = compose(before, smem[w]);
+    Map excl = shfl_up_map(incl, 1);
+    if (lane == 0) excl = identity;
+    __syncthreads();  // smem reusable
+    return compose(before, excl);
+}
+
+struct Mm1Sums128 {
+    U128 w, i, v;
+};
+
+__device__ __forceinline__ U128 shfl_down_u128(const U128& x, int off) {
+    U128 r;
+    r.lo = __shfl_down_sync(kFull, x.lo, off);
+    r.hi = __shfl_down_sync(kFull, x.hi, off);
+    return r;
+}
+__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
+    a.lo += b.lo;
+    a.hi += b.hi + ((a.lo < b.lo) ? 1u : 0u);
+}
+
+__global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict__ dps, long long n_reps,
+                                                       long long n_clients, bool staged,
+                                                       const __grid_constant__ RoundKeys rk, LogTable tab,
+                                                       Mm1Out out) {
+    extern __shared__ long long fix_stage[];  // [client - lo][thread] x (S, A) when staged
+    __shared__ FixMap fmaps[32];
+    __shared__ DblMap dmaps[32];
+    __shared__ U128 part[3][32];
+    __shared__ double dpart[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const long long item = blockIdx.x;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    const uint32_t c3 = stream_word(0u, dp);
+    const long long k = (n_clients + blockDim.x - 1) / blockDim.x;
+    const long long lo = min(static_cast<long long>(threadIdx.x) * k, n_clients);
+    const long long hi = min(lo + k, n_clients);
+    const double inv_n = static_cast<double>(n_clients);
+
+    bool fixed_ok = fix_rate_ok(lam) && fix_rate_ok(mu);
+    if (fixed_ok) {
+        const unsigned long long cl = fix_scale(lam), cmu = fix_scale(mu);
+        FixMap f{-kSat, 0};
+        long long* st_s = fix_stage + threadIdx.x;
+        long long* st_a = fix_stage + k * blockDim.x + threadIdx.x;
+        for (long long n = lo; n < hi; ++n) {
+            const uint4 b = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const long long sv = to_fix(neg_log_q57(word_k(b.x, b.y), tab), cmu);
+            const long long av = to_fix(neg_log_q57(word_k(b.z, b.w), tab), cl);
+            if (staged) {
+                st_s[(n - lo) * blockDim.x] = sv;
+                st_a[(n - lo) * blockDim.x] = av;
+            }
+            f = fcompose(f, FixMap{0, sv - av});
+        }
+        const FixMap pre = block_exclusive_map(f, FixMap{-kSat, 0}, fmaps, fcompose);
+        long long w = pre.c > pre.d ? pre.c : pre.d;  // map at W_0 = 0
+        if (threadIdx.x == 0) w = 0;
+        bool bad = w >= kFixGuard;
+        Mm1Sums128 sm;
+        for (long long n = lo; n < hi && !bad; ++n) {
+            long long sv, av;
+            if (staged) {
+                sv = st_s[(n - lo) * blockDim.x];
+                av = st_a[(n - lo) * blockDim.x];
+            } else {
+                const uint4 b = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+                sv = to_fix(neg_log_q57(word_k(b.x, b.y), tab), cmu);
+                av = to_fix(neg_log_q57(word_k(b.z, b.w), tab), cl);
+            }
+            sm.w.add(w);
+            const long long v = w + sv;
+            sm.v.add(v);
+            const long long t = v - av;
+            sm.i.add(t < 0 ? -t : 0);
+            w = t > 0 ? t : 0;
+            bad = w >= kFixGuard;
+        }
+        fixed_ok = !__syncthreads_or(bad);
+        if (fixed_ok) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                add_u128(sm.w, shfl_down_u128(sm.w, off));
+                add_u128(sm.i, shfl_down_u128(sm.i, off));
+                add_u128(sm.v, shfl_down_u128(sm.v, off));
+            }
+            if (lane == 0) {
+                part[0][warp] = sm.w;
+                part[1][warp] = sm.i;
+                part[2][warp] = sm.v;
+            }
+            __syncthreads();
+            if (threadIdx.x < 3) {
+                U128 tot;
+                for (int x = 0; x < nwarp; ++x) add_u128(tot, part[threadIdx.x][x]);
+                double* dst = threadIdx.x == 0 ? out.wait : threadIdx.x == 1 ? out.idle : out.system;
+                if (dst) dst[item] = tot.to_double() / inv_n;
+            }
+            return;
+        }
+    }
+    // FP64: the same passes with doubles
+    const double inv_lam = 0x1p-57 / lam, inv_mu = 0x1p-57 / mu;
+    DblMap f{-INFINITY, 0.0};
+    for (long long n = lo; n < hi; ++n) {
+        double sv, av;
+        mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, sv, av);
+        f = dcompose(f, DblMap{0.0, sv - av});
+    }
+    const DblMap pre = block_exclusive_map(f, DblMap{-INFINITY, 0.0}, dmaps, dcompose);
+    double w = pre.c > pre.d ? pre.c : pre.d;
+    if (threadIdx.x == 0) w = 0.0;
+    double sw = 0.0, si = 0.0, sv_sum = 0.0;
+    for (long long n = lo; n < hi; ++n) {
+        double sv, av;
+        mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, sv, av);
+        sw += w;
+        const double v = w + sv;
+        sv_sum += v;
+        const double t = v - av;
+        si += (t < 0.0) ? -t : 0.0;
+        w = (t > 0.0) ? t : 0.0;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {  // lane-ordered tree
+        const double ow = __shfl_down_sync(kFull, sw, off);
+        const double oi = __shfl_down_sync(kFull, si, off);
+        const double ov = __shfl_down_sync(kFull, sv_sum, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            sw += ow;
+            si += oi;
+            sv_sum += ov;
+        }
+    }
+    if (lane == 0) {
+        dpart[0][warp] = sw;
+        dpart[1][warp] = si;
+        dpart[2][warp] = sv_sum;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double tot = 0.0;
+        for (int x = 0; x < nwarp; ++x) tot += dpart[threadIdx.x][x];
+        double* dst = threadIdx.x == 0 ? out.wait : threadIdx.x == 1 ? out.idle : out.system;
+        if (dst) dst[item] = tot / inv_n;
+    }
+}
+
 }  // namespace
 }  // namespace mrip
 
@@ -529,6 +724,17 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         mm1_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
             d_dps, n_items, n_reps, n_clients, rk, tab, out);
+    } else if (mapping == MRIP_MAP_CTA) {
+        if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_mm1_simulate: too many replications for CTA");
+        // about 4 clients per thread, 32 .. 1024 threads; fixed-point variates
+        // staged in shared memory between the passes when they fit 48 KiB
+        long long threads = ((n_clients + 3) / 4 + 31) / 32 * 32;
+        threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+        const long long per_thread = (n_clients + threads - 1) / threads;
+        const size_t stage = static_cast<size_t>(threads * per_thread) * 2 * sizeof(long long);
+        const bool staged = stage <= 48 * 1024;
+        mm1_cta_kernel<<<static_cast<unsigned>(n_items), static_cast<unsigned>(threads), staged ? stage : 0, st>>>(
+            d_dps, n_reps, n_clients, staged, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_COOP) {
         const long long seg = (n_clients + 31) / 32;
         const size_t per_warp = static_cast<size_t>(seg) * 32 * 2 * sizeof(double);
@@ -546,7 +752,7 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
                 d_dps, n_items, n_reps, n_clients, rk, tab, out);
         }
     } else {
-        return fail(MRIP_EINVAL, "mrip_mm1_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: mapping must be THREAD, WARP_1LANE, WARP_COOP or CTA");
     }
     return launch_status("mrip_mm1_simulate");
 }

@@ -84,7 +84,7 @@ def test_expo_variates(eng, torch_mod):
 MM1_DPS = np.array([[0.9, 1.0], [0.5, 1.0], [1.2, 1.0]])
 
 
-@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP"])
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP", "CTA"])
 @pytest.mark.parametrize("n_clients", [1, 31, 1000, 1337])
 def test_mm1_all_mappings(eng, torch_mod, mapping, n_clients):
     t = torch_mod
@@ -96,6 +96,23 @@ def test_mm1_all_mappings(eng, torch_mod, mapping, n_clients):
     ref = oracle.mm1(MM1_DPS, *items, n_clients, 42, threads=threads())
     for g, r in zip(out, ref):
         np.testing.assert_allclose(g.cpu().numpy(), r, rtol=REL, atol=1e-300)
+
+
+@pytest.mark.parametrize("n_clients", [5000, 100003])
+def test_mm1_cta_fallbacks(eng, torch_mod, n_clients):
+    """One replication per CTA with a block scan of fixed-point maps: slow
+    rates (below 2^-6) and a queue whose wait passes 2^12 redo the
+    replication in FP64; ~4 clients per thread up to 1,024 threads, then
+    longer segments."""
+    t = torch_mod
+    dps = np.array([[0.9, 1.0], [0.005, 0.01], [3.0, 1.0], [0.5, 16.0]])
+    n_reps = 5
+    out = [t.empty(4 * n_reps, dtype=t.float64, device="cuda") for _ in range(3)]
+    eng.mrip_mm1_simulate(dev(t, dps), n_reps, n_clients, 42, eng.MRIP_MAP_CTA, *out)
+    ref = oracle.mm1(dps, *oracle.all_items(4, n_reps), n_clients, 42, threads=threads())
+    for g, r in zip(out, ref):
+        np.testing.assert_allclose(g.cpu().numpy(), r, rtol=REL, atol=1e-300)
+    assert ref[0][2 * n_reps:3 * n_reps].min() > 4096 / 4  # the unstable point really grows
 
 
 def test_mm1_workload_full(eng, torch_mod):
