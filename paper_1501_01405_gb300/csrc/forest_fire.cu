@@ -52,11 +52,14 @@ __device__ __forceinline__ StepKey step_key(uint32_t t, uint32_t rep, const Roun
     return s;
 }
 
-__device__ __forceinline__ uint4 philox_step(uint32_t c0, uint32_t c3, const StepKey& sk,
+// prod = 0xD2511F53 * c0 as a 64-bit product (round 1's only varying product);
+// the 8 blocks of one lattice word have c0 = 8k + q, so the caller forms it
+// as 0xD2511F53 * 8k plus a constant: one 64-bit add instead of a wide
+// multiply for 7 of every 8 blocks.
+__device__ __forceinline__ uint4 philox_step(unsigned long long prod, uint32_t c3, const StepKey& sk,
                                              const RoundKeys& rk) {
-    // round 1: only the product with c0 varies
-    const uint32_t a_hi = __umulhi(0xD2511F53u, c0);
-    const uint32_t a_lo = 0xD2511F53u * c0;
+    const uint32_t a_hi = static_cast<uint32_t>(prod >> 32);
+    const uint32_t a_lo = static_cast<uint32_t>(prod);
     const uint32_t w2 = a_hi ^ c3 ^ rk.k1[0];
     // round 2: the product with word 0 is sk.p
     const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2);
@@ -201,9 +204,10 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
             const uint32_t beast = cur_b[y * W + ((j + 1) & (W - 1))];
             const uint32_t nb = up | dn | (bw << 1) | (bwest >> 31) | (bw >> 1) | (beast << 31);
             uint32_t g = 0, l = 0;
+            const unsigned long long base = 0xD2511F53ull * (8u * static_cast<uint32_t>(k));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const uint4 b = philox_step(8u * k + q, c3, sk, rk);
+                const uint4 b = philox_step(base + 0xD2511F53ull * q, c3, sk, rk);
                 g |= (b.x < t_grow) ? (1u << (4 * q)) : 0u;
                 g |= (b.y < t_grow) ? (1u << (4 * q + 1)) : 0u;
                 g |= (b.z < t_grow) ? (1u << (4 * q + 2)) : 0u;
