@@ -12,6 +12,9 @@
 // (Horner) in double-double, and solved by a bracketed Newton iteration
 // whose density comes from lgamma.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -146,7 +149,7 @@ double density(double t, long long nu) {
 
 }  // namespace
 
-double t_critical(double conf, long long df) {
+double t_critical_uncached(double conf, long long df) {
     const double tail = (1.0 - conf) / 2.0;
     double lo = 0.0, hi = 1.0;
     while (upper_tail(hi, df) > tail) {
@@ -169,6 +172,25 @@ double t_critical(double conf, long long df) {
         }
         t = next;
     }
+    return t;
+}
+
+// The series has about df/2 terms per evaluation and the solve takes a few
+// dozen evaluations, so large df cost milliseconds; repeated runs of one
+// experiment ask for the same (conf, df), so results are kept (bounded).
+double t_critical(double conf, long long df) {
+    static std::mutex mu;
+    static std::map<std::pair<double, long long>, double> cache;
+    const std::pair<double, long long> key(conf, df);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const double t = t_critical_uncached(conf, df);
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() >= 4096) cache.clear();
+    cache.emplace(key, t);
     return t;
 }
 

@@ -14,7 +14,10 @@
 // Mappings:
 //   PERSISTENT  #SM x k CTAs; each warp takes chunks of replications from a
 //               global ticket (atomicAdd) and refills a lane as soon as its
-//               walker exits, so lanes stay busy despite uneven lengths.
+//               walker exits, so lanes stay busy despite uneven lengths;
+//               words that may cross the boundary are walked by the whole
+//               warp (walk_block_warp), so one lane near the boundary does
+//               not serialise the other 31.
 //   THREAD      one replication per thread (TLP), no refill.
 //   WARP_1LANE  one replication per warp, lane 0 only (the paper's WLP).
 //   WARP_COOP   one replication per warp: the 32 lanes take 32 consecutive
@@ -95,6 +98,81 @@ __device__ __forceinline__ bool walk_block(const uint4 b, int R, int& x, int& y,
     return false;
 }
 
+// Warp-convergent block step for the persistent mapping, in the diagonal
+// coordinates u = x + y, v = x - y (|x| + |y| = max(|u|, |v|); a move changes
+// u by +1 iff its bit 0 is clear and v by +1 iff its two bits agree).  Per
+// 16-move word, a lane whose walker cannot leave within the word -- u plus
+// the word's +1 steps in u below R, u minus its -1 steps above -R, the same
+// for v -- applies the word at once (popcounts).  The other lanes' words are
+// then walked by the whole warp, two lanes at a time: each half-warp takes
+// one walker's 16 moves, one per lane, a 16-lane scan gives the positions
+// and a ballot the first exit.
+// This keeps the per-move work off the warp when one lane of 32 is near the
+// boundary, which (with stopping times spread over orders of magnitude) is
+// most of the time.  `live`: the lane has a walker; on return `done` marks
+// walkers that exited in this block (m = tau).
+__device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R, int& u, int& v, long long& m,
+                                                bool& done) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t words[4] = {b.x, b.y, b.z, b.w};
+    done = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t w = words[k];
+        const uint32_t b0 = w & kEven;
+        const uint32_t b01 = (w ^ (w >> 1)) & kEven;
+        const int mu = __popc(b0), mv = __popc(b01);  // -1 steps of u, of v
+        const bool going = live && !done;
+        const bool safe = u + (16 - mu) < R && u - mu > -R && v + (16 - mv) < R && v - mv > -R;
+        if (going && safe) {
+            u += 16 - 2 * mu;
+            v += 16 - 2 * mv;
+            m += 16;
+        }
+        unsigned near = __ballot_sync(kFull, going && !safe);
+        while (near) {  // two walkers per pass: lanes 0..15 and 16..31
+            const int src0 = __ffs(near) - 1;
+            near &= near - 1;
+            int src1 = -1;
+            if (near) {
+                src1 = __ffs(near) - 1;
+                near &= near - 1;
+            }
+            const int src = (lane >= 16 && src1 >= 0) ? src1 : src0;
+            const uint32_t ws = __shfl_sync(kFull, w, src);
+            const int us = __shfl_sync(kFull, u, src), vs = __shfl_sync(kFull, v, src);
+            const int rs = __shfl_sync(kFull, R, src);
+            const uint32_t f = (ws >> (2 * (lane & 15))) & 3u;
+            int du = 1 - 2 * static_cast<int>(f & 1u);
+            int dv = 1 - 2 * static_cast<int>((f ^ (f >> 1)) & 1u);
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {
+                const int pu = __shfl_up_sync(kFull, du, off, 16);
+                const int pv = __shfl_up_sync(kFull, dv, off, 16);
+                if ((lane & 15) >= off) {
+                    du += pu;
+                    dv += pv;
+                }
+            }
+            const unsigned hits = __ballot_sync(kFull, max(abs(us + du), abs(vs + dv)) >= rs);
+            const int tu0 = __shfl_sync(kFull, du, 15), tv0 = __shfl_sync(kFull, dv, 15);
+            const int tu1 = __shfl_sync(kFull, du, 31), tv1 = __shfl_sync(kFull, dv, 31);
+            const bool me0 = lane == src0, me1 = lane == src1;
+            if (me0 || me1) {
+                const unsigned h = me0 ? (hits & 0xFFFFu) : (hits >> 16);
+                if (h) {
+                    m += __ffs(h);
+                    done = true;
+                } else {
+                    u += me0 ? tu0 : tu1;
+                    v += me0 ? tv0 : tv1;
+                    m += 16;
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void decode(const WalkJob& job, long long g, int& R, uint32_t& dp,
                                        uint32_t& rep, long long& out) {
     const long long k = g / job.n_reps;
@@ -143,7 +221,7 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     bool active = false;
-    int x = 0, y = 0, R = 0;
+    int u = 0, v = 0, R = 1;
     long long m = 0, out = 0;
     uint32_t dp = 0, rep = 0, c3 = 0;
     long long next = 0, end = 0;  // warp-uniform range of the current chunk
@@ -167,8 +245,8 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
             if (take) {
                 decode(job, g, R, dp, rep, out);
                 c3 = stream_word(0u, dp);
-                x = 0;
-                y = 0;
+                u = 0;
+                v = 0;
                 m = 0;
                 active = true;
             }
@@ -177,9 +255,11 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
             need &= ~took;
         }
         if (!__any_sync(kFull, active)) break;
+        const uint4 b = philox(0u, static_cast<uint32_t>(m >> 6), rep, c3, rk);
+        bool done;
+        walk_block_warp(b, active, R, u, v, m, done);
         if (active) {
-            const uint4 b = philox(0u, static_cast<uint32_t>(m >> 6), rep, c3, rk);
-            if (walk_block(b, R, x, y, m)) {
+            if (done) {
                 if (m > job.max_steps) {
                     job.tau[out] = -1;
                     atomicExch(job.err, 1);
@@ -262,7 +342,7 @@ mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_p
     job.n_reps = n_reps;
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
-    job.chunk = chunk > 0 ? chunk : 64;
+    job.chunk = chunk > 0 ? chunk : 16;
     job.tau = d_tau;
     job.ticket = d_ticket;
     job.err = device_error_flags();
@@ -271,7 +351,7 @@ mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_p
     if (job.total == 0) return MRIP_OK;
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_PERSISTENT) {
         const int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
-        const int cps = ctas_per_sm > 0 ? ctas_per_sm : 4;
+        const int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
         if (wpc > 32 || cps > 64) return fail(MRIP_EINVAL, "walk: warps_per_cta <= 32, ctas_per_sm <= 64");
         if (!d_ticket) return fail(MRIP_EINVAL, "walk: persistent mapping needs a ticket counter");
         cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
@@ -414,7 +494,7 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     job.n_reps = n_reps;
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
-    job.chunk = chunk > 0 ? chunk : 64;
+    job.chunk = chunk > 0 ? chunk : 16;
     job.tau = d_tau;
     job.ticket = reinterpret_cast<unsigned long long*>(base);
     job.err = reinterpret_cast<int*>(base + 8);
