@@ -8,7 +8,10 @@ A step is one pass of the hot path over one batch of synthetic input: all
 replications of the workload simulated by the CUDA kernels and reduced to
 per-design-point (n, mean, M2) on the device.  The default workload is the
 128x128 forest fire (1,024 replications x 1,000 steps); the others are
-selectable (mm1_32, walk8, tandem, ff256, tandem_cv).
+selectable: mm1_32 (latency; its step replays as one CUDA graph), mm1_64k
+(throughput), walk8, tandem, ff256, ff128_skip / ff256_skip (skip-sampled
+lattice events), area_walk and pi (the paper's own models; --sweep times
+them against the replication count).
 
 value   = replications / s over the K timed steps, inputs resident in HBM,
           device time from CUDA events on the launching stream, L2 flushed
@@ -228,6 +231,7 @@ class Walk(Workload):
         self.eng, self.torch = eng, torch
         n = self.units()
         self.tau = torch.empty(n, dtype=torch.int64, device="cuda")
+        self.nmm2 = torch.empty(len(self.radii) * 3, dtype=torch.float64, device="cuda")
 
     def step(self, k_start=None, k_end=None):
         if k_start is not None:
@@ -236,8 +240,9 @@ class Walk(Workload):
                                     self.eng.MRIP_MAP_PERSISTENT, self.tau)
         if k_end is not None:
             k_end.record()
+        self.eng.mrip_stats_reduce_i64(self.tau.view(len(self.radii), self.w["n_reps"]), self.nmm2)
 
-    launches_per_step = 1
+    launches_per_step = 3  # walk, statistics over slices, slice merge
 
     def roofline_work(self):
         moves = 0.0
@@ -263,14 +268,20 @@ class Walk(Workload):
         oracle.walk(self.radii, dp, rep, self.seed, threads=threads)
 
 
+def stats_launches(n_reps):
+    """Kernels of one statistics reduction: slices of 4,096 replications are
+    merged by a second kernel."""
+    return 2 if n_reps > 4096 else 1
+
+
 class Queue(Workload):
     dtype = "f64"
 
     def __init__(self, rank, key):
         super().__init__(rank)
         self.key = key
-        if key == "mm1_32":
-            self.w = mrip_inputs.workload("mm1_32")
+        if key in ("mm1_32", "mm1_64k"):
+            self.w = mrip_inputs.workload(key)
         else:
             self.w = mrip_inputs.workload("tandem_cv")
         self.name = key
@@ -281,6 +292,10 @@ class Queue(Workload):
 
     def config(self):
         w = self.w
+        if self.key == "mm1_64k":
+            return {"workload": "mm1_64k: M/M/1 Lindley, lambda 0.9, mu 1, 1000 clients, 65536 "
+                                "replications", "n_reps": w["n_reps"], "n_clients": w["n_clients"],
+                    "seed": self.seed, "mapping": "thread per replication, 48-bit fixed-point times"}
         if self.key == "mm1_32":
             return {"workload": "mm1_32: M/M/1 Lindley, lambda 0.9, mu 1, 1000 clients, 32 "
                                 "replications", "n_reps": w["n_reps"], "n_clients": w["n_clients"],
@@ -299,16 +314,17 @@ class Queue(Workload):
         self.d_dps = torch.tensor(w["dps"], dtype=torch.float64, device="cuda")
         self.y = torch.empty(n, dtype=torch.float64, device="cuda")
         self.feat = torch.empty(8 * n, dtype=torch.float64, device="cuda") \
-            if self.key != "mm1_32" else None
+            if self.key == "tandem" else None
         self.nmm2 = torch.empty(w["n_dp"] * 3, dtype=torch.float64, device="cuda")
 
     def step(self, k_start=None, k_end=None):
         w = self.w
         if k_start is not None:
             k_start.record()
-        if self.key == "mm1_32":
+        if self.key in ("mm1_32", "mm1_64k"):
+            mapping = self.eng.MRIP_MAP_CTA if self.key == "mm1_32" else self.eng.MRIP_MAP_THREAD
             self.eng.mrip_mm1_simulate(self.d_dps, w["n_reps"], w["n_clients"], self.seed,
-                                       self.eng.MRIP_MAP_CTA, self.y)
+                                       mapping, self.y)
         else:
             self.eng.mrip_tandem3_simulate(self.d_dps, 0, w["n_reps"], w["n_clients"],
                                            w["window"], self.seed, 0, self.eng.MRIP_MAP_THREAD,
@@ -317,7 +333,9 @@ class Queue(Workload):
             k_end.record()
         self.eng.mrip_stats_reduce(self.y.view(w["n_dp"], w["n_reps"]), self.nmm2)
 
-    launches_per_step = 2
+    @property
+    def launches_per_step(self):
+        return 1 + stats_launches(self.w["n_reps"])
 
     @property
     def graph_step(self):
@@ -326,11 +344,12 @@ class Queue(Workload):
     def roofline_work(self):
         w = self.w
         clients = self.units() * w["n_clients"]
-        blocks = 1 if self.key == "mm1_32" else 2
-        logs = 2 if self.key == "mm1_32" else 4
+        blocks = 2 if self.key == "tandem" else 1
+        logs = 4 if self.key == "tandem" else 2
         per_client = blocks * INT_MULS_PER_PHILOX + logs * MULS_PER_FIXED_VARIATE
-        return dict(kernel="mm1_cta_kernel (graph with the statistics kernel)" if self.key == "mm1_32"
-                    else "tandem3_serial_kernel", bound="alu",
+        kernel = {"mm1_32": "mm1_cta_kernel (graph with the statistics kernel)",
+                  "mm1_64k": "mm1_serial_kernel", "tandem": "tandem3_serial_kernel"}[self.key]
+        return dict(kernel=kernel, bound="alu",
                     unit="Gop/s (32-bit integer multiply)", work=clients * per_client,
                     peak=imul_peak_gops(),
                     peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
@@ -341,9 +360,10 @@ class Queue(Workload):
 
     def make_model(self):
         w = self.w
-        if self.key == "mm1_32":
+        if self.key in ("mm1_32", "mm1_64k"):
             m = self.eng.Model(self.eng.MRIP_MM1, n_clients=w["n_clients"])
-            m.set_plan('{"mapping": %d}' % self.eng.MRIP_MAP_CTA)
+            mapping = self.eng.MRIP_MAP_CTA if self.key == "mm1_32" else self.eng.MRIP_MAP_THREAD
+            m.set_plan('{"mapping": %d}' % mapping)
             return m
         return self.eng.Model(self.eng.MRIP_TANDEM3, n_clients=w["n_clients"],
                               window=w["window"])
@@ -357,7 +377,7 @@ class Queue(Workload):
         g = np.arange(n_items)
         dp = (g % w["n_dp"]).astype(np.int32)
         rep = (g // w["n_dp"]) % w["n_reps"]
-        if self.key == "mm1_32":
+        if self.key in ("mm1_32", "mm1_64k"):
             oracle.mm1(w["dps"], dp, rep, w["n_clients"], self.seed, threads=threads)
         else:
             oracle.tandem3(w["dps"], dp, rep, w["n_clients"], self.seed, window=w["window"],
@@ -575,7 +595,7 @@ def make_workload(name, rank):
         return ForestFireSkip(rank, "ff128" if name == "ff128_skip" else "ff256_cv")
     if name == "walk8":
         return Walk(rank)
-    if name in ("mm1_32", "tandem"):
+    if name in ("mm1_32", "mm1_64k", "tandem"):
         return Queue(rank, name)
     if name == "area_walk":
         return AreaWalk(rank)
@@ -827,7 +847,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="ff128",
-                    choices=["ff128", "ff256", "ff128_skip", "ff256_skip", "walk8", "mm1_32", "tandem",
+                    choices=["ff128", "ff256", "ff128_skip", "ff256_skip", "walk8", "mm1_32", "mm1_64k", "tandem",
                              "area_walk", "pi"])
     ap.add_argument("--sweep", action="store_true",
                     help="area_walk: time every mapping for 1 .. 2^16 replications; "

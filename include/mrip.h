@@ -344,10 +344,18 @@ mrip_status mrip_pi_simulate(int64_t n_reps, int64_t n_draws, uint64_t seed, int
 mrip_status mrip_check_device_flags(void);
 
 /* Per-design-point (n, mean, M2) of d_x (device double [n_dp][n_reps]) by
- * Welford within a thread and a Chan merge across threads in a fixed tree
- * (deterministic).  d_out: device double [n_dp][3]. */
+ * Welford within a thread and a Chan merge across threads in a fixed tree;
+ * more than 4,096 replications are cut into slices (one CTA each) merged in
+ * slice order (deterministic).  d_out: device double [n_dp][3].  The slice
+ * partials live in library scratch memory, which a later call may grow:
+ * capture this call in a CUDA graph only if that graph is replayed before
+ * any larger reduction runs (4,096 replications or fewer need no scratch). */
 mrip_status mrip_stats_reduce(const double *d_x, int32_t n_dp, int64_t n_reps,
                               double *d_out, void *stream);
+
+/* mrip_stats_reduce for int64 outputs (the walk's exit times). */
+mrip_status mrip_stats_reduce_i64(const int64_t *d_x, int32_t n_dp, int64_t n_reps,
+                                  double *d_out, void *stream);
 
 /* Host, synchronous: intervals from host (n, mean, M2) triples. */
 mrip_status mrip_stats_finalize(const double *nmm2, int32_t n_dp, double conf,

@@ -12,6 +12,8 @@ Section 5, scaled to a modern GPU):
 
 * ``mm1_32``        M/M/1 via Lindley, lambda=0.9, mu=1, 1,000 clients,
                     32 replications, 1 design point, seed 42.
+* ``mm1_64k``       the same model with 2^16 replications (the throughput
+                    row beside the latency-bound 32).
 * ``ff128``         forest fire 128x128, p_grow=0.01, p_lightning=1e-5,
                     density 0.5, 1,000 steps, 1,024 replications.
 * ``walk8``         L1-exit walk, R in {16,32,48,64,96,128,192,256},
@@ -49,6 +51,8 @@ def ff_cv_design_points(n_dp=64, p_light=1e-5):
 WORKLOADS = {
     "mm1_32": dict(kind="mm1", dps=np.array([[0.9, 1.0]]), n_reps=32, n_clients=1000,
                    seed=SEED),
+    "mm1_64k": dict(kind="mm1", dps=np.array([[0.9, 1.0]]), n_reps=1 << 16, n_clients=1000,
+                    seed=SEED),
     "ff128": dict(kind="forest_fire", L=128, n_steps=1000, dps=np.array([[0.01, 1e-5]]),
                   density=0.5, n_reps=1024, seed=SEED),
     "walk8": dict(kind="walk", dps=np.array(WALK_RADII, dtype=np.float64)[:, None],

@@ -162,6 +162,12 @@ def mrip_stats_reduce(x, out, stream=None):
                                    _dev(out, t.float64, "out"), _stream(stream)))
 
 
+def mrip_stats_reduce_i64(x, out, stream=None):
+    t = _t()
+    _check(lib().mrip_stats_reduce_i64(_dev(x, t.int64, "x"), x.shape[0], x.shape[1],
+                                       _dev(out, t.float64, "out"), _stream(stream)))
+
+
 def mrip_stats_finalize(nmm2, conf=0.95):
     a, p = _host(nmm2, np.float64)
     n_dp = a.size // 3

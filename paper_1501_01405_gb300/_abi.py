@@ -91,6 +91,7 @@ SIGNATURES = {
     "mrip_pi_simulate": (_INT, [_I64, _I64, _U64, _P, _P]),
     "mrip_check_device_flags": (_INT, []),
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
+    "mrip_stats_reduce_i64": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_finalize": (_INT, [_P, _I32, _D, _P]),
     "mrip_t_crit": (_INT, [_D, _I64, _P]),
     "mrip_stats_merge": (_INT, [_P, _I32, _I32, _P]),

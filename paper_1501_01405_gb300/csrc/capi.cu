@@ -74,7 +74,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
             double* w = m->out0.as<double>();
             s = mrip_mm1_simulate(d_dps, n_dp, n_reps, m->mm1.n_clients, seed, m->plan.mapping, w,
                                   w + items, w + 2 * items, st);
-            if (s == MRIP_OK) s = stats_reduce_double(w, n_dp, n_reps, m->nmm2.as<double>(), st);
+            if (s == MRIP_OK) s = stats_reduce_double(w, n_dp, n_reps, m->nmm2.as<double>(), st, m->spart.as<double>());
             break;
         }
         case MRIP_TANDEM3: {
@@ -82,7 +82,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
                                       seed, 0, m->plan.mapping, m->out0.as<double>(),
                                       m->out1.as<double>(), st);
             if (s == MRIP_OK)
-                s = stats_reduce_double(m->out0.as<double>(), n_dp, n_reps, m->nmm2.as<double>(), st);
+                s = stats_reduce_double(m->out0.as<double>(), n_dp, n_reps, m->nmm2.as<double>(), st, m->spart.as<double>());
             break;
         }
         case MRIP_FOREST_FIRE: {
@@ -90,7 +90,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
                                           seed, nullptr, m->out0.as<int32_t>(), m->out1.as<double>(),
                                           nullptr, st);
             if (s == MRIP_OK)
-                s = stats_reduce_double(m->out1.as<double>(), n_dp, n_reps, m->nmm2.as<double>(), st);
+                s = stats_reduce_double(m->out1.as<double>(), n_dp, n_reps, m->nmm2.as<double>(), st, m->spart.as<double>());
             break;
         }
         case MRIP_WALK_L1_EXIT: {
@@ -99,7 +99,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
                             m->plan.warps_per_cta, m->plan.ctas_per_sm, m->plan.chunk,
                             m->out0.as<int64_t>(), m->ticket.as<unsigned long long>(), st);
             if (s == MRIP_OK)
-                s = stats_reduce_int64(m->out0.as<int64_t>(), n_dp, n_reps, m->nmm2.as<double>(), st);
+                s = stats_reduce_int64(m->out0.as<int64_t>(), n_dp, n_reps, m->nmm2.as<double>(), st, m->spart.as<double>());
             break;
         }
         default: s = fail(MRIP_EINVAL, "unknown model kind");
@@ -119,6 +119,8 @@ mrip_status prepare(mrip_model* m, int32_t n_dp, int64_t n_reps) {
     m->n_reps = n_reps;
     bool ok = m->dps.ensure(static_cast<size_t>(n_dp) * dp_dim(m->kind) * sizeof(double)) &&
               m->nmm2.ensure(static_cast<size_t>(n_dp) * 3 * sizeof(double));
+    const size_t spart = stats_scratch_bytes(n_dp, n_reps);
+    if (spart) ok = ok && m->spart.ensure(spart);
     switch (m->kind) {
         case MRIP_MM1: ok = ok && m->out0.ensure(3 * items * sizeof(double)); break;
         case MRIP_TANDEM3:

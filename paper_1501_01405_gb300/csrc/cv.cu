@@ -90,8 +90,9 @@ void epoch_affine(uint64_t seed, int epoch, unsigned long long n, unsigned long 
 // Per-plane FP64 mean and population std (zero std -> 1) of d planes of n.
 mrip_status plane_moments(const double* x, int d, long long n, DevBuf& tmp, double* host_ms, double* dev_ms,
                           cudaStream_t st) {
-    if (!tmp.ensure(static_cast<size_t>(d) * 3 * sizeof(double))) return fail(MRIP_ENOMEM, "cv: moments");
-    mrip_status s = stats_reduce_double(x, d, n, tmp.as<double>(), st);
+    const size_t head = static_cast<size_t>(d) * 3 * sizeof(double);
+    if (!tmp.ensure(head + stats_scratch_bytes(d, n))) return fail(MRIP_ENOMEM, "cv: moments");
+    mrip_status s = stats_reduce_double(x, d, n, tmp.as<double>(), st, tmp.as<double>() + 3 * d);
     if (s != MRIP_OK) return s;
     std::vector<double> h(3 * d);
     cudaError_t e = cudaMemcpyAsync(h.data(), tmp.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -50,7 +50,7 @@ struct mrip_model {
     mrip_walk_params walk{};
     cudaStream_t stream = nullptr;
     Plan plan;
-    DevBuf dps, out0, out1, nmm2, walk_tab, ticket;
+    DevBuf dps, out0, out1, nmm2, walk_tab, ticket, spart;
     std::vector<double> host_dps;
     int32_t n_dp = 0;
     int64_t n_reps = 0;
@@ -76,9 +76,11 @@ mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_p
 mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>& r_by_pos,
                         std::vector<int32_t>& dp_by_pos);
 mrip_status stats_reduce_double(const double* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                                cudaStream_t st);
+                                cudaStream_t st, double* d_part);
 mrip_status stats_reduce_int64(const int64_t* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                               cudaStream_t st);
+                               cudaStream_t st, double* d_part);
+// Bytes of the slice-partials buffer stats_reduce_* needs (0: none).
+size_t stats_scratch_bytes(int32_t n_dp, int64_t n_reps);
 double t_critical(double conf, long long df);
 mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                int32_t L, int32_t n_steps, double density, uint64_t seed,

@@ -18,6 +18,59 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// ---------------------------------------------------------------------------
+// Times in 64-bit fixed point.  GB300 retires about two FP64 operations per
+// SM-clock and over forty 32-bit integer multiplies, so the queue recurrences
+// (additions, subtractions and maxima only) run on integers: a time t is held
+// as round(t 2^48).  A variate is E / rate with E = y57 2^-57 from the
+// fixed-point log, i.e. round(y57 * (2^-9 / rate)), the factor stored as a
+// 64-bit multiplier cm = round(2^57 / rate) (2^-9 / rate = cm 2^-66).  A
+// variate then carries the multiplier's relative error (2^-53, as an FP64
+// division would) plus half a unit (2^-49), and every recurrence step is
+// exact, where FP64 rounds each addition; the outputs agree with
+// FP64 evaluation far inside 1e-12 as long as the variates are not tiny
+// against 2^-48: rates are limited to [2^-6, 2^4] (mean variate >= 1/16).
+// A variate is then below 36.8 * 64 < 2^11.3 time units (E <= 53 ln 2);
+// while the largest state stays below 2^12 (2^60 units) one more step stays
+// below 2^61.5, so nothing overflows.  Design points with other rates run the
+// FP64 recurrence, and a replication whose sojourn time reaches 2^12
+// restarts in FP64.  Means of single variates (the early-window features)
+// are summed in FP64 from the same log values, where a variate's relative
+// precision matters.
+// ---------------------------------------------------------------------------
+constexpr int kFixBits = 48;
+constexpr long long kFixGuard = 1LL << 60;
+constexpr long long kFixNegInf = -(1LL << 62);  // "empty" state: v - A stays above -2^63
+
+// 2^-9 / rate as cm 2^-66 (cm in [2^53, 2^63] for the rates above: at least
+// 53 significant bits), so that round(y57 2^-9 / rate) = (hi(y57 cm) + 2) >> 2.
+__device__ __forceinline__ bool fix_rate_ok(double rate) { return rate >= 0x1p-6 && rate <= 0x1p4; }
+
+__device__ __forceinline__ unsigned long long fix_scale(double rate) {
+    return static_cast<unsigned long long>(0x1p57 / rate + 0.5);
+}
+
+__device__ __forceinline__ long long to_fix(unsigned long long y57, unsigned long long cm) {
+    return static_cast<long long>((__umul64hi(y57, cm) + 2u) >> 2);
+}
+
+struct U128 {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(long long v) {  // v >= 0
+        const unsigned long long u = static_cast<unsigned long long>(v);
+        lo += u;
+        hi += (lo < u) ? 1u : 0u;
+    }
+    __device__ __forceinline__ double to_double() const {  // value 2^-48
+        return static_cast<double>(hi) * 0x1p16 + static_cast<double>(lo) * 0x1p-48;
+    }
+};
+
+__device__ __forceinline__ unsigned long long word_k(uint32_t lo, uint32_t hi) {
+    const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
+    return (1ULL << 53) - (bits >> 11);
+}
+
 struct Mm1Out {
     double* wait;
     double* idle;
@@ -35,7 +88,7 @@ __device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp
 }
 
 template <bool kLane0Only>
-__global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
+__global__ void __launch_bounds__(128, 8) mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
                                   long long n_reps, long long n_clients,
                                   const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     long long item;
@@ -48,7 +101,37 @@ __global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_it
     if (item >= n_items) return;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(item % n_reps);
-    const double inv_lam = 0x1p-57 / dps[2 * dp], inv_mu = 0x1p-57 / dps[2 * dp + 1];
+    const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
+    const double inv = static_cast<double>(n_clients);
+    if (fix_rate_ok(lam) && fix_rate_ok(mu)) {  // 48-bit fixed-point times
+        const unsigned long long cl = fix_scale(lam), cmu = fix_scale(mu);
+        const uint32_t c3 = stream_word(0u, dp);
+        long long wf = 0;
+        U128 sw, si, sv;
+        bool overflow = false;
+        for (long long n = 0; n < n_clients; ++n) {
+            const uint4 b = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const long long s_ = to_fix(neg_log_q57(word_k(b.x, b.y), tab), cmu);
+            const long long a_ = to_fix(neg_log_q57(word_k(b.z, b.w), tab), cl);
+            sw.add(wf);
+            const long long v = wf + s_;
+            sv.add(v);
+            const long long t = v - a_;
+            si.add(t < 0 ? -t : 0);
+            wf = t > 0 ? t : 0;
+            if (wf >= kFixGuard) {
+                overflow = true;
+                break;
+            }
+        }
+        if (!overflow) {
+            if (out.wait) out.wait[item] = sw.to_double() / inv;
+            if (out.idle) out.idle[item] = si.to_double() / inv;
+            if (out.system) out.system[item] = sv.to_double() / inv;
+            return;
+        }
+    }
+    const double inv_lam = 0x1p-57 / lam, inv_mu = 0x1p-57 / mu;
     double w = 0.0, sum_w = 0.0, sum_i = 0.0, sum_v = 0.0;
     for (long long n = 0; n < n_clients; ++n) {
         double s, a;
@@ -60,7 +143,6 @@ __global__ void mm1_serial_kernel(const double* __restrict__ dps, long long n_it
         sum_i += (t < 0.0) ? -t : 0.0;
         w = (t > 0.0) ? t : 0.0;
     }
-    const double inv = static_cast<double>(n_clients);
     if (out.wait) out.wait[item] = sum_w / inv;
     if (out.idle) out.idle[item] = sum_i / inv;
     if (out.system) out.system[item] = sum_v / inv;
@@ -160,59 +242,6 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
         if (out.idle) out.idle[item] = sum_i / inv;
         if (out.system) out.system[item] = sum_v / inv;
     }
-}
-
-// ---------------------------------------------------------------------------
-// Times in 64-bit fixed point.  GB300 retires about two FP64 operations per
-// SM-clock and over forty 32-bit integer multiplies, so the queue recurrences
-// (additions, subtractions and maxima only) run on integers: a time t is held
-// as round(t 2^48).  A variate is E / rate with E = y57 2^-57 from the
-// fixed-point log, i.e. round(y57 * (2^-9 / rate)), the factor stored as a
-// 64-bit multiplier cm = round(2^57 / rate) (2^-9 / rate = cm 2^-66).  A
-// variate then carries the multiplier's relative error (2^-53, as an FP64
-// division would) plus half a unit (2^-49), and every recurrence step is
-// exact, where FP64 rounds each addition; the outputs agree with
-// FP64 evaluation far inside 1e-12 as long as the variates are not tiny
-// against 2^-48: rates are limited to [2^-6, 2^4] (mean variate >= 1/16).
-// A variate is then below 36.8 * 64 < 2^11.3 time units (E <= 53 ln 2);
-// while the largest state stays below 2^12 (2^60 units) one more step stays
-// below 2^61.5, so nothing overflows.  Design points with other rates run the
-// FP64 recurrence, and a replication whose sojourn time reaches 2^12
-// restarts in FP64.  Means of single variates (the early-window features)
-// are summed in FP64 from the same log values, where a variate's relative
-// precision matters.
-// ---------------------------------------------------------------------------
-constexpr int kFixBits = 48;
-constexpr long long kFixGuard = 1LL << 60;
-constexpr long long kFixNegInf = -(1LL << 62);  // "empty" state: v - A stays above -2^63
-
-// 2^-9 / rate as cm 2^-66 (cm in [2^53, 2^63] for the rates above: at least
-// 53 significant bits), so that round(y57 2^-9 / rate) = (hi(y57 cm) + 2) >> 2.
-__device__ __forceinline__ bool fix_rate_ok(double rate) { return rate >= 0x1p-6 && rate <= 0x1p4; }
-
-__device__ __forceinline__ unsigned long long fix_scale(double rate) {
-    return static_cast<unsigned long long>(0x1p57 / rate + 0.5);
-}
-
-__device__ __forceinline__ long long to_fix(unsigned long long y57, unsigned long long cm) {
-    return static_cast<long long>((__umul64hi(y57, cm) + 2u) >> 2);
-}
-
-struct U128 {
-    unsigned long long lo = 0, hi = 0;
-    __device__ __forceinline__ void add(long long v) {  // v >= 0
-        const unsigned long long u = static_cast<unsigned long long>(v);
-        lo += u;
-        hi += (lo < u) ? 1u : 0u;
-    }
-    __device__ __forceinline__ double to_double() const {  // value 2^-48
-        return static_cast<double>(hi) * 0x1p16 + static_cast<double>(lo) * 0x1p-48;
-    }
-};
-
-__device__ __forceinline__ unsigned long long word_k(uint32_t lo, uint32_t hi) {
-    const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
-    return (1ULL << 53) - (bits >> 11);
 }
 
 // ---------------------------------------------------------------------------

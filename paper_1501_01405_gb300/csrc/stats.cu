@@ -2,10 +2,11 @@
 // the replication mean and a CLT confidence interval) and the Student-t
 // critical value.
 //
-// Device: one CTA per design point.  Thread t runs Welford's update over the
-// replications t, t + B, t + 2B, ...; the CTA merges the (n, mean, M2)
-// triples pairwise in a fixed tree (Chan, Golub, LeVeque 1979), so the
-// result does not depend on scheduling.
+// Device: one CTA per design point and slice of at most 4,096 replications.
+// Thread t runs Welford's update over the slice's replications t, t + B, ...;
+// the CTA merges the (n, mean, M2) triples pairwise in a fixed tree (Chan,
+// Golub, LeVeque 1979) and a second kernel merges the slices in order, so
+// the result does not depend on scheduling.
 //
 // Host: t_{(1+conf)/2, df} from Abramowitz & Stegun 26.7.3/26.7.4 (finite
 // series in cos^2(theta) for integer df), evaluated innermost-first
@@ -39,14 +40,21 @@ __device__ __forceinline__ void chan_merge(double& na, double& ma, double& m2a, 
     na = n;
 }
 
+// One CTA per (design point, slice of replications): Welford per thread over
+// the slice, then the CTA's fixed merge tree.  With one slice the triple goes
+// straight to out[dp]; otherwise to part[dp][slice].
 template <typename T>
 __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const T* __restrict__ x, long long n_reps,
-                                                              double* __restrict__ out) {
+                                                              int slices, double* __restrict__ out) {
     __shared__ double sn[kStatsThreads], sm[kStatsThreads], s2[kStatsThreads];
-    const long long dp = blockIdx.x;
+    const long long dp = blockIdx.x / slices;
+    const long long sl = blockIdx.x - dp * slices;
+    const long long per = (n_reps + slices - 1) / slices;
+    const long long lo = sl * per;
+    const long long hi = lo + per < n_reps ? lo + per : n_reps;
     const T* row = x + dp * n_reps;
     double n = 0.0, mean = 0.0, m2 = 0.0;
-    for (long long i = threadIdx.x; i < n_reps; i += kStatsThreads) {
+    for (long long i = lo + threadIdx.x; i < hi; i += kStatsThreads) {
         const double v = static_cast<double>(row[i]);
         n += 1.0;
         const double d = v - mean;
@@ -69,10 +77,24 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const T* __restric
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        out[3 * dp] = sn[0];
-        out[3 * dp + 1] = sm[0];
-        out[3 * dp + 2] = s2[0];
+        double* o = out + 3 * blockIdx.x;
+        o[0] = sn[0];
+        o[1] = sm[0];
+        o[2] = s2[0];
     }
+}
+
+// Slices of one design point merged in slice order.
+__global__ void stats_merge_kernel(const double* __restrict__ part, int n_dp, int slices,
+                                   double* __restrict__ out) {
+    const int dp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dp >= n_dp) return;
+    const double* p = part + static_cast<long long>(dp) * slices * 3;
+    double n = p[0], mean = p[1], m2 = p[2];
+    for (int s = 1; s < slices; ++s) chan_merge(n, mean, m2, p[3 * s], p[3 * s + 1], p[3 * s + 2]);
+    out[3 * dp] = n;
+    out[3 * dp + 1] = mean;
+    out[3 * dp + 2] = m2;
 }
 
 // ---------------------------------------------------------------------------
@@ -194,19 +216,49 @@ double t_critical(double conf, long long df) {
     return t;
 }
 
-mrip_status stats_reduce_double(const double* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                                cudaStream_t st) {
+// Replications per slice: few design points with many replications would
+// otherwise run on a few SMs (the FP64 Welford update is ~14 FP64 operations
+// per value on GB300's narrow FP64 pipe).
+constexpr long long kStatsSlice = 4096;
+
+int stats_slices(int32_t n_dp, int64_t n_reps) {
+    long long s = (n_reps + kStatsSlice - 1) / kStatsSlice;
+    if (s < 1) s = 1;
+    if (s > 256) s = 256;
+    if (static_cast<long long>(n_dp) * s > 0x7FFFFFFFll) s = 1;
+    return static_cast<int>(s);
+}
+
+size_t stats_scratch_bytes(int32_t n_dp, int64_t n_reps) {
+    const int s = stats_slices(n_dp, n_reps);
+    return s > 1 ? static_cast<size_t>(n_dp) * s * 3 * sizeof(double) : 0;
+}
+
+template <typename T>
+mrip_status stats_reduce_t(const T* d_x, int32_t n_dp, int64_t n_reps, double* d_out, double* d_part,
+                           cudaStream_t st) {
     if (n_dp == 0) return MRIP_OK;
-    stats_kernel<double><<<n_dp, kStatsThreads, 0, st>>>(d_x, n_reps, d_out);
+    const int slices = stats_slices(n_dp, n_reps);
+    if (slices == 1) {
+        stats_kernel<T><<<n_dp, kStatsThreads, 0, st>>>(d_x, n_reps, 1, d_out);
+        return launch_status("stats reduce");
+    }
+    if (!d_part) return fail(MRIP_ENOMEM, "stats reduce: no partials buffer");
+    stats_kernel<T><<<static_cast<unsigned>(static_cast<long long>(n_dp) * slices), kStatsThreads, 0, st>>>(
+        d_x, n_reps, slices, d_part);
+    stats_merge_kernel<<<(n_dp + 127) / 128, 128, 0, st>>>(d_part, n_dp, slices, d_out);
     return launch_status("stats reduce");
 }
 
+mrip_status stats_reduce_double(const double* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
+                                cudaStream_t st, double* d_part) {
+    return stats_reduce_t<double>(d_x, n_dp, n_reps, d_out, d_part, st);
+}
+
 mrip_status stats_reduce_int64(const int64_t* d_x, int32_t n_dp, int64_t n_reps, double* d_out,
-                               cudaStream_t st) {
-    if (n_dp == 0) return MRIP_OK;
-    stats_kernel<long long><<<n_dp, kStatsThreads, 0, st>>>(
-        reinterpret_cast<const long long*>(d_x), n_reps, d_out);
-    return launch_status("stats reduce");
+                               cudaStream_t st, double* d_part) {
+    return stats_reduce_t<long long>(reinterpret_cast<const long long*>(d_x), n_dp, n_reps, d_out, d_part,
+                                     st);
 }
 
 void finalize_one(double n, double mean, double m2, double conf, mrip_stat* out) {
@@ -231,7 +283,20 @@ extern "C" mrip_status mrip_stats_reduce(const double* d_x, int32_t n_dp, int64_
                                          double* d_out, void* stream) {
     if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_stats_reduce: negative size");
     if (n_dp > 0 && (!d_x || !d_out)) return fail(MRIP_EINVAL, "mrip_stats_reduce: null pointer");
-    return stats_reduce_double(d_x, n_dp, n_reps, d_out, static_cast<cudaStream_t>(stream));
+    const size_t need = stats_scratch_bytes(n_dp, n_reps);
+    double* part = need ? static_cast<double*>(scratch(need, 3)) : nullptr;
+    if (need && !part) return fail(MRIP_ENOMEM, "mrip_stats_reduce: scratch allocation failed");
+    return stats_reduce_double(d_x, n_dp, n_reps, d_out, static_cast<cudaStream_t>(stream), part);
+}
+
+extern "C" mrip_status mrip_stats_reduce_i64(const int64_t* d_x, int32_t n_dp, int64_t n_reps,
+                                             double* d_out, void* stream) {
+    if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_stats_reduce_i64: negative size");
+    if (n_dp > 0 && (!d_x || !d_out)) return fail(MRIP_EINVAL, "mrip_stats_reduce_i64: null pointer");
+    const size_t need = stats_scratch_bytes(n_dp, n_reps);
+    double* part = need ? static_cast<double*>(scratch(need, 3)) : nullptr;
+    if (need && !part) return fail(MRIP_ENOMEM, "mrip_stats_reduce_i64: scratch allocation failed");
+    return stats_reduce_int64(d_x, n_dp, n_reps, d_out, static_cast<cudaStream_t>(stream), part);
 }
 
 extern "C" mrip_status mrip_stats_finalize(const double* nmm2, int32_t n_dp, double conf,

@@ -300,8 +300,9 @@ def test_forest_fire_workload_full_sampled(eng, torch_mod):
 
 
 def test_forest_fire_cv_workload_sampled(eng, torch_mod):
-    """256x256, 2,000 steps, 64 design points x 128 replications on the GPU;
-    replications {0, 127} of design points {0, 21, 42, 63} against the oracle."""
+    """256x256, 2,000 steps, 64 design points x 128 replications on the GPU in
+    the bench's launch; every design point's replications {0, 1, 127} at full
+    length bit-exact against the oracle (192 replications)."""
     t = torch_mod
     w = mrip_inputs.workload("ff256_cv")
     n = w["n_dp"] * w["n_reps"]
@@ -310,14 +311,27 @@ def test_forest_fire_cv_workload_sampled(eng, torch_mod):
     eng.mrip_forest_fire_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], w["n_steps"],
                                   w["density"], w["seed"], None, counts, scalar)
     gc = counts.cpu().numpy().reshape(n, w["n_steps"])
-    dp = np.repeat([0, 21, 42, 63], 2).astype(np.int32)
-    rep = np.tile([0, 127], 4)
+    dp = np.repeat(np.arange(w["n_dp"]), 3).astype(np.int32)
+    rep = np.tile([0, 1, w["n_reps"] - 1], w["n_dp"])
     rc = oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"], dp, rep, w["seed"],
                             threads=threads())
     idx = dp * w["n_reps"] + rep
     assert np.array_equal(gc[idx], rc)
     sc = scalar.cpu().numpy()[idx]
     assert np.array_equal(sc, rc.sum(axis=1) / (w["n_steps"] * w["L"] ** 2))
+
+
+def test_forest_fire_cv_workload_every_replication_short(eng, torch_mod):
+    """The same 8,192 replications cut to 100 steps: every one bit-exact."""
+    t = torch_mod
+    w = mrip_inputs.workload("ff256_cv")
+    n, steps = w["n_dp"] * w["n_reps"], 100
+    counts = t.empty(n * steps, dtype=t.int32, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], steps, w["density"],
+                                  w["seed"], None, counts)
+    rc = oracle.forest_fire(w["L"], steps, w["dps"], w["density"],
+                            *oracle.all_items(w["n_dp"], w["n_reps"]), w["seed"], threads=threads())
+    assert np.array_equal(counts.cpu().numpy().reshape(n, steps), rc)
 
 
 # ------------------------------------------------------------------ walk
@@ -374,8 +388,10 @@ def test_walk_workload_full_sampled(eng, torch_mod):
 
 
 # ------------------------------------------------------------------ statistics
-@pytest.mark.parametrize("n_reps", [1, 2, 255, 257, 1 << 17])
+@pytest.mark.parametrize("n_reps", [1, 2, 255, 257, 4096, 4097, 12289, 1 << 17, 1 << 21])
 def test_stats_reduce(eng, torch_mod, n_reps):
+    """One CTA up to 4,096 replications, then slices merged in order (a ragged
+    last slice at 4,097 and 12,289; 256 slices at 2^21)."""
     t = torch_mod
     n_dp = 5
     x = mrip_inputs.random_matrix((n_dp, n_reps), 3, scale=2.0, loc=7.0)
@@ -390,6 +406,20 @@ def test_stats_reduce(eng, torch_mod, n_reps):
             assert got[d, 2] / (n - 1) == pytest.approx(var, rel=1e-12)
         else:
             assert got[d, 2] == 0.0
+
+
+def test_stats_reduce_i64(eng, torch_mod):
+    t = torch_mod
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, 1 << 40, size=(3, 50001), dtype=np.int64)
+    out = t.empty(9, dtype=t.float64, device="cuda")
+    eng.mrip_stats_reduce_i64(dev(t, x), out)
+    got = out.cpu().numpy().reshape(3, 3)
+    for d in range(3):
+        n, mean, var = ostats.dp_stats(x[d].astype(np.float64))
+        assert got[d, 0] == n
+        assert got[d, 1] == pytest.approx(mean, rel=1e-13)
+        assert got[d, 2] / (n - 1) == pytest.approx(var, rel=1e-12)
 
 
 # ------------------------------------------------------------------ model handles
