@@ -140,6 +140,16 @@ class ForestFire(Workload):
                         SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
                     per_unit="10 int multiplies per cell-update (1/4 Philox block)")
 
+    def extra_rates(self, reps_per_s, torch):
+        w = self.w
+        cells = float(w["L"] * w["L"] * w["n_steps"])
+        # algorithmic HBM traffic: the int32 burning count of every step and the
+        # FP64 scalar per replication written, the design points read
+        bytes_per_rep = 4.0 * w["n_steps"] + 8.0 + 16.0 / w["n_reps"]
+        return {"cell_updates_per_s": reps_per_s * cells,
+                "hbm_gbs_algorithmic": reps_per_s * bytes_per_rep / 1e9,
+                "hbm_note": "low by construction: the lattice lives in shared memory"}
+
     def make_model(self):
         w = self.w
         m = self.eng.Model(self.eng.MRIP_FOREST_FIRE, L=w["L"], n_steps=w["n_steps"],
@@ -244,6 +254,10 @@ class Walk(Workload):
 
     launches_per_step = 3  # walk, statistics over slices, slice merge
 
+    def extra_rates(self, reps_per_s, torch):
+        moves = float(self.tau.double().sum().item())  # every replication's exit time
+        return {"moves_per_s": reps_per_s * moves / self.units(), "moves_per_step": moves}
+
     def roofline_work(self):
         moves = 0.0
         for R in mrip_inputs.WALK_RADII:
@@ -336,6 +350,11 @@ class Queue(Workload):
     @property
     def launches_per_step(self):
         return 1 + stats_launches(self.w["n_reps"])
+
+    def extra_rates(self, reps_per_s, torch):
+        clients = reps_per_s * self.w["n_clients"]
+        return {"clients_per_s": clients,
+                "exponential_variates_per_s": clients * (4 if self.key == "tandem" else 2)}
 
     @property
     def graph_step(self):
@@ -978,15 +997,21 @@ def main():
             "gpu_launches": wl.launches_per_step * args.steps,
             "wall_s": t_wall}
 
+    extra = wl.extra_rates(value, torch) if hasattr(wl, "extra_rates") else None
+    if extra:
+        line["rates"] = extra
     if rank == 0 and world == 1 and not args.no_cv:
         line["time_to_target"] = time_to_target(eng, torch, stream, 42)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = oracle.host_threads()
         n, s = time_oracle(wl, args.cpu_seconds, threads)
+        n1, s1 = time_oracle(wl, max(1.0, args.cpu_seconds / 4), 1)
         line["cpu_baseline"] = {"value": n / s, "unit": "replications/s", "cores": threads,
                                 "kind": "oracle",
-                                "sample": "%d replications of %s in %.1f s" % (n, wl.name, s)}
+                                "sample": "%d replications of %s in %.1f s" % (n, wl.name, s),
+                                "single_thread": {"value": n1 / s1, "unit": "replications/s",
+                                                  "sample": "%d replications in %.1f s" % (n1, s1)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -66,6 +66,21 @@ struct U128 {
     }
 };
 
+constexpr long long kSat = 1LL << 61;
+
+__device__ __forceinline__ long long sat61(long long x) { return x > kSat ? kSat : (x < -kSat ? -kSat : x); }
+
+__device__ __forceinline__ U128 shfl_down_u128(const U128& x, int off) {
+    U128 r;
+    r.lo = __shfl_down_sync(kFull, x.lo, off);
+    r.hi = __shfl_down_sync(kFull, x.hi, off);
+    return r;
+}
+__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
+    a.lo += b.lo;
+    a.hi += b.hi + ((a.lo < b.lo) ? 1u : 0u);
+}
+
 __device__ __forceinline__ unsigned long long word_k(uint32_t lo, uint32_t hi) {
     const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
     return (1ULL << 53) - (bits >> 11);
@@ -434,6 +449,63 @@ __device__ __forceinline__ TandemClient tandem_client(uint32_t n, uint32_t rep, 
                         expo_fast(b1.x, b1.y, tab, i_mu2), expo_fast(b1.z, b1.w, tab, i_mu3)};
 }
 
+// The same maps in 48-bit fixed point, every sum saturated at +-2^61 (the
+// empty state's -inf is -2^61).  After one client every constant is positive,
+// so a term pushed down to -2^61 never decides a maximum for states in
+// [0, 2^60]; a state or constant past 2^60 sends the replication to FP64.
+struct FTMap {
+    long long c1, c2, c3, d11, d21, d22, d31, d32, d33;
+};
+
+__device__ __forceinline__ FTMap ftmap_identity() {
+    return FTMap{-kSat, -kSat, -kSat, 0, -kSat, 0, -kSat, -kSat, 0};
+}
+
+__device__ __forceinline__ long long lmax(long long x, long long y) { return x > y ? x : y; }
+
+__device__ __forceinline__ FTMap ftmap_push(const FTMap& f, long long a, long long s1, long long s2, long long s3) {
+    const long long e1 = s1 - a, e2 = s2 - a, e3 = s3 - a;
+    FTMap r;
+    r.c1 = lmax(s1, sat61(f.c1 + e1));
+    r.d11 = sat61(f.d11 + e1);
+    r.c2 = sat61(lmax(f.c2 + e2, r.c1 + s2));
+    r.d21 = sat61(lmax(f.d21 + e2, r.d11 + s2));
+    r.d22 = sat61(f.d22 + e2);
+    r.c3 = sat61(lmax(f.c3 + e3, r.c2 + s3));
+    r.d31 = sat61(lmax(f.d31 + e3, r.d21 + s3));
+    r.d32 = sat61(lmax(f.d32 + e3, r.d22 + s3));
+    r.d33 = sat61(f.d33 + e3);
+    return r;
+}
+
+__device__ __forceinline__ FTMap ftmap_compose(const FTMap& f, const FTMap& g) {  // g after f
+    FTMap h;
+    h.c1 = lmax(g.c1, sat61(f.c1 + g.d11));
+    h.c2 = lmax(g.c2, sat61(lmax(f.c1 + g.d21, f.c2 + g.d22)));
+    h.c3 = lmax(g.c3, sat61(lmax(f.c1 + g.d31, lmax(f.c2 + g.d32, f.c3 + g.d33))));
+    h.d11 = sat61(f.d11 + g.d11);
+    h.d21 = sat61(lmax(f.d11 + g.d21, f.d21 + g.d22));
+    h.d22 = sat61(f.d22 + g.d22);
+    h.d31 = sat61(lmax(f.d11 + g.d31, lmax(f.d21 + g.d32, f.d31 + g.d33)));
+    h.d32 = sat61(lmax(f.d22 + g.d32, f.d32 + g.d33));
+    h.d33 = sat61(f.d33 + g.d33);
+    return h;
+}
+
+__device__ __forceinline__ FTMap ftmap_shfl_up(const FTMap& m, int off) {
+    FTMap r;
+    r.c1 = __shfl_up_sync(kFull, m.c1, off);
+    r.c2 = __shfl_up_sync(kFull, m.c2, off);
+    r.c3 = __shfl_up_sync(kFull, m.c3, off);
+    r.d11 = __shfl_up_sync(kFull, m.d11, off);
+    r.d21 = __shfl_up_sync(kFull, m.d21, off);
+    r.d22 = __shfl_up_sync(kFull, m.d22, off);
+    r.d31 = __shfl_up_sync(kFull, m.d31, off);
+    r.d32 = __shfl_up_sync(kFull, m.d32, off);
+    r.d33 = __shfl_up_sync(kFull, m.d33, off);
+    return r;
+}
+
 __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
     const double* __restrict__ dps, long long n_items, long long n_reps, long long rep0,
     long long n_clients, long long window, uint32_t tag, const __grid_constant__ RoundKeys rk,
@@ -452,7 +524,92 @@ __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
     const long long lo = min(lane * seg, n_clients);
     const long long hi = min(lo + seg, n_clients);
 
-    // pass 1: this segment's map
+    if (fix_rate_ok(lam) && fix_rate_ok(mu1) && fix_rate_ok(mu2) && fix_rate_ok(mu3)) {
+        const unsigned long long cl = fix_scale(lam), c1 = fix_scale(mu1), c2 = fix_scale(mu2),
+                                 c3f = fix_scale(mu3);
+        FTMap f = ftmap_identity();
+        for (long long n = lo; n < hi; ++n) {
+            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            f = ftmap_push(f, to_fix(neg_log_q57(word_k(b0.x, b0.y), tab), cl),
+                           to_fix(neg_log_q57(word_k(b0.z, b0.w), tab), c1),
+                           to_fix(neg_log_q57(word_k(b1.x, b1.y), tab), c2),
+                           to_fix(neg_log_q57(word_k(b1.z, b1.w), tab), c3f));
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const FTMap prev = ftmap_shfl_up(f, off);
+            if (lane >= off) f = ftmap_compose(prev, f);
+        }
+        const FTMap excl = ftmap_shfl_up(f, 1);
+        long long v1 = kFixNegInf, v2 = kFixNegInf, v3 = kFixNegInf;
+        if (lane > 0) {
+            v1 = excl.c1;
+            v2 = excl.c2;
+            v3 = excl.c3;
+        }
+        bool bad = v3 >= kFixGuard;
+        U128 sy;
+        double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        for (long long n = lo; n < hi && !bad; ++n) {
+            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            const unsigned long long ya = neg_log_q57(word_k(b0.x, b0.y), tab);
+            const unsigned long long y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
+            const unsigned long long y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
+            const unsigned long long y3 = neg_log_q57(word_k(b1.z, b1.w), tab);
+            const long long a = to_fix(ya, cl);
+            long long q = v1 - a;
+            v1 = ((q > 0) ? q : 0) + to_fix(y1, c1);
+            q = v2 - a;
+            v2 = ((q > v1) ? q : v1) + to_fix(y2, c2);
+            q = v3 - a;
+            v3 = ((q > v2) ? q : v2) + to_fix(y3, c3f);
+            sy.add(v3);
+            if (n < w_len) {
+                wa += __ull2double_rn(ya) * i_lam;
+                w1 += __ull2double_rn(y1) * i_mu1;
+                w2 += __ull2double_rn(y2) * i_mu2;
+                w3 += __ull2double_rn(y3) * i_mu3;
+            }
+            bad = v3 >= kFixGuard;
+        }
+        if (!__any_sync(kFull, bad)) {
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {  // lane-ordered tree (integers: exact)
+                const U128 oy = shfl_down_u128(sy, off);
+                const double oa = __shfl_down_sync(kFull, wa, off);
+                const double o1 = __shfl_down_sync(kFull, w1, off);
+                const double o2 = __shfl_down_sync(kFull, w2, off);
+                const double o3 = __shfl_down_sync(kFull, w3, off);
+                if ((lane & (2 * off - 1)) == 0) {
+                    add_u128(sy, oy);
+                    wa += oa;
+                    w1 += o1;
+                    w2 += o2;
+                    w3 += o3;
+                }
+            }
+            if (lane != 0) return;
+            out.y[item] = sy.to_double() / static_cast<double>(n_clients);
+            if (out.feat) {
+                const double wl = static_cast<double>(w_len);
+                double* fo = out.feat + item;
+                const long long p = out.plane;
+                fo[0] = lam;
+                fo[p] = mu1;
+                fo[2 * p] = mu2;
+                fo[3 * p] = mu3;
+                fo[4 * p] = wa / wl;
+                fo[5 * p] = w1 / wl;
+                fo[6 * p] = w2 / wl;
+                fo[7 * p] = w3 / wl;
+            }
+            return;
+        }
+    }
+
+    // FP64: pass 1, this segment's map
     TMap f = tmap_identity();
     for (long long n = lo; n < hi; ++n) {
         const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
@@ -536,9 +693,6 @@ __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
 // then, or for rates outside [2^-6, 2^4], the CTA redoes the replication in
 // FP64 with the same structure (maps with -inf, sums in a fixed tree).
 // ---------------------------------------------------------------------------
-constexpr long long kSat = 1LL << 61;
-
-__device__ __forceinline__ long long sat61(long long x) { return x > kSat ? kSat : (x < -kSat ? -kSat : x); }
 
 struct FixMap {
     long long c, d;
@@ -585,16 +739,6 @@ struct Mm1Sums128 {
     U128 w, i, v;
 };
 
-__device__ __forceinline__ U128 shfl_down_u128(const U128& x, int off) {
-    U128 r;
-    r.lo = __shfl_down_sync(kFull, x.lo, off);
-    r.hi = __shfl_down_sync(kFull, x.hi, off);
-    return r;
-}
-__device__ __forceinline__ void add_u128(U128& a, const U128& b) {
-    a.lo += b.lo;
-    a.hi += b.hi + ((a.lo < b.lo) ? 1u : 0u);
-}
 
 __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict__ dps, long long n_reps,
                                                        long long n_clients, bool staged,

@@ -149,7 +149,7 @@ def test_tandem_thread_and_wlp(eng, torch_mod):
         np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, ref_f, rtol=REL)
 
 
-@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE"])
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP"])
 def test_tandem_fixed_point_fallbacks(eng, torch_mod, mapping):
     """Times run in 48-bit fixed point; a slow rate (below 2^-6) sends a design
     point to FP64 and an unstable queue whose sojourn time passes 2^12
