@@ -140,8 +140,8 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const long long items = static_cast<long long>(n_dp) * n_reps;
     const double cells = tandem ? 0.0 : static_cast<double>(m->ff.L) * m->ff.L;
 
-    DevBuf feat_all, y_all_ff, x_tr, y_tr, x_ho, y_ho, ms_dev, tmp, xs_tr, ys_tr, xs_ho, g_ho, g_hod, theta, mom, vel,
-        partial, losses, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
+    DevBuf feat_all, y_all_ff, x_tr, y_tr, x_ho, y_ho, ms_dev, tmp, xs_tr, ys_tr, xs_ho, g_ho, g_hod, theta, sched,
+        losses, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
     const double* feat_src;  // d_in planes of `items`
     const double* y_src;     // items
     if (tandem) {
@@ -190,33 +190,34 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const long long B = p->batch;
     const long long steps_per_epoch = (n_tr + B - 1) / B;
     const long long n_steps = steps_per_epoch * p->epochs;
-    if (!theta.ensure(P * sizeof(float)) || !mom.ensure(P * sizeof(float)) || !vel.ensure(P * sizeof(float)) ||
-        !partial.ensure(mlp_grad_partial_floats(d_in, B) * sizeof(float)) ||
-        !losses.ensure(n_steps * sizeof(float)))
+    // per epoch the affine order (a, b), per step Adam's bias corrections,
+    // computed here in double and rounded to float as the stage entry points
+    // take them; then all epochs in one cluster launch
+    std::vector<unsigned long long> ab(2 * static_cast<size_t>(p->epochs));
+    for (int ep = 0; ep < p->epochs; ++ep)
+        epoch_affine(p->net_seed, ep, static_cast<unsigned long long>(n_tr), ab[2 * ep], ab[2 * ep + 1]);
+    std::vector<float> bc(2 * static_cast<size_t>(n_steps));
+    for (long long k = 1; k <= n_steps; ++k) {
+        bc[2 * (k - 1)] = static_cast<float>(1.0 - std::pow(static_cast<double>(p->beta1), static_cast<double>(k)));
+        bc[2 * (k - 1) + 1] =
+            static_cast<float>(1.0 - std::pow(static_cast<double>(p->beta2), static_cast<double>(k)));
+    }
+    const size_t ab_bytes = ab.size() * sizeof(unsigned long long);
+    if (!theta.ensure(P * sizeof(float)) || !losses.ensure(n_steps * sizeof(float)) ||
+        !sched.ensure(ab_bytes + bc.size() * sizeof(float)))
         return fail(MRIP_ENOMEM, "cv: network buffers");
-    cudaError_t e = cudaMemsetAsync(mom.p, 0, P * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(vel.p, 0, P * sizeof(float), st);
-    if (e != cudaSuccess) return cuda_status(e, "cv: optimiser state");
+    cudaError_t e = cudaMemcpyAsync(sched.p, ab.data(), ab_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char*>(sched.p) + ab_bytes, bc.data(), bc.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (e != cudaSuccess) return cuda_status(e, "cv: training schedule");
     s = mlp_init(d_in, p->net_seed, theta.as<float>(), st);
     if (s != MRIP_OK) return s;
-    long long step = 0;
-    for (int ep = 0; ep < p->epochs; ++ep) {
-        unsigned long long a, b;
-        epoch_affine(p->net_seed, ep, static_cast<unsigned long long>(n_tr), a, b);
-        for (long long off = 0; off < n_tr; off += B) {
-            const long long nb = (off + B <= n_tr) ? B : n_tr - off;
-            ++step;
-            const double bc1 = 1.0 - std::pow(static_cast<double>(p->beta1), static_cast<double>(step));
-            const double bc2 = 1.0 - std::pow(static_cast<double>(p->beta2), static_cast<double>(step));
-            const float adam[6] = {p->lr, p->beta1, p->beta2, p->eps, static_cast<float>(bc1),
-                                   static_cast<float>(bc2)};
-            s = mlp_step(theta.as<float>(), d_in, xs_tr.as<float>(), n_tr, ys_tr.as<float>(), nullptr, a, b,
-                         static_cast<unsigned long long>(n_tr), off, nb, partial.as<float>(), nullptr,
-                         losses.as<float>() + (step - 1), theta.as<float>(), mom.as<float>(), vel.as<float>(),
-                         adam, st);
-            if (s != MRIP_OK) return s;
-        }
-    }
+    s = mlp_train(d_in, xs_tr.as<float>(), ys_tr.as<float>(), n_tr, B, p->epochs, sched.as<unsigned long long>(),
+                  reinterpret_cast<const float*>(static_cast<char*>(sched.p) + ab_bytes), p->lr, p->beta1,
+                  p->beta2, p->eps, theta.as<float>(), losses.as<float>(), st);
+    if (s != MRIP_OK) return s;
     if (loss_out) {
         std::vector<float> hl(steps_per_epoch);
         e = cudaMemcpyAsync(hl.data(), losses.as<float>() + (n_steps - steps_per_epoch),

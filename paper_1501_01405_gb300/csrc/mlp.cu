@@ -17,6 +17,7 @@
 // consecutive words), and writes its per-parameter partial sums; a second
 // kernel adds the partials of all CTAs in a fixed order (deterministic) and,
 // during training, applies Adam in the same pass.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -86,35 +87,32 @@ __device__ __forceinline__ long long sample_of(const SampleMap& m, long long i) 
     return static_cast<long long>(k);
 }
 
+constexpr int HP = H + 4;
+
 struct GradSmem {
-    float w1t[kMaxIn][H];  // [k][u]
-    float w2t[H][H];       // [u][v]
-    float w2[H][H];        // [v][u]
+    alignas(16) float w1t[kMaxIn][H];  // [k][u]
+    alignas(16) float w2t[H][H];       // [u][v]
+    alignas(16) float w2[H][H];        // [v][u]
     float w3[H], b1[H], b2[H];
     float b3;
     float xt[kTile][kMaxIn];
-    float h1[kTile][H];
-    float h1t[kTile][H];
-    float h2[kTile][H];
-    float h2t[kTile][H];
-    float dz2[kTile][H];
-    float dz2t[kTile][H];
-    float dz1[kTile][H];
+    // per-sample rows padded to HP words: samples 4 apart in a warp sit in
+    // different banks, and rows stay 16-byte aligned for float4 loads
+    alignas(16) float h1[kTile][HP];
+    alignas(16) float h1t[kTile][HP];
+    alignas(16) float h2[kTile][HP];
+    alignas(16) float h2t[kTile][HP];
+    alignas(16) float dz2[kTile][HP];
+    alignas(16) float dz2t[kTile][HP];
+    alignas(16) float dz1[kTile][HP];
     float dy[kTile];
     float ys[kTile];
 };
 
-// Forward + backward of one tile of kTile samples; partial[blockIdx][p] gets
-// the tile's gradient, partial_loss[blockIdx] its sum of squared residuals.
-__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
-    const float* __restrict__ theta, int d_in, const float* __restrict__ X, long long n_total,
-    const float* __restrict__ Y, SampleMap map, long long B, float* __restrict__ partial,
-    float* __restrict__ partial_loss) {
-    extern __shared__ unsigned char smem_raw[];
-    GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+// Stage the BF16-rounded weights (and FP32 biases) of theta (global or
+// shared) into S.
+__device__ void stage_weights(GradSmem& S, const float* theta, int d_in) {
     const int t = threadIdx.x;
-    const long long P = n_params(d_in);
-
     for (int i = t; i < H * d_in; i += kGradThreads) {
         const int u = i / d_in, k = i - u * d_in;
         S.w1t[k][u] = bf(theta[i]);
@@ -131,16 +129,27 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
         S.b2[i] = theta[off_b2(d_in) + i];
     }
     if (t == 0) S.b3 = theta[off_b3(d_in)];
-    const long long base = static_cast<long long>(blockIdx.x) * kTile;
+}
+
+// Stage samples at batch positions pos0 .. pos0 + n_valid - 1 (n_valid <= kTile;
+// the rest of the tile is zero and contributes nothing).
+__device__ void stage_tile(GradSmem& S, int d_in, const float* __restrict__ X, long long n_total,
+                           const float* __restrict__ Y, const SampleMap& map, long long pos0, int n_valid) {
+    const int t = threadIdx.x;
     for (int i = t; i < kTile * kMaxIn; i += kGradThreads) {
         const int s = i / kMaxIn, k = i - s * kMaxIn;
         float v = 0.0f;
-        if (base + s < B && k < d_in) v = bf(X[k * n_total + sample_of(map, base + s)]);
+        if (s < n_valid && k < d_in) v = bf(X[k * n_total + sample_of(map, pos0 + s)]);
         S.xt[s][k] = v;
     }
-    if (t < kTile) S.ys[t] = (base + t < B) ? Y[sample_of(map, base + t)] : 0.0f;
-    __syncthreads();
+    if (t < kTile) S.ys[t] = (t < n_valid) ? Y[sample_of(map, pos0 + t)] : 0.0f;
+}
 
+// Forward and backward passes of the staged tile (batch size B_scale for the
+// loss gradient 2 r / B).  Leaves h1, h2, dz1, dz2, dy and the squared
+// residuals (in ys) in S.
+__device__ void tile_passes(GradSmem& S, int d_in, int n_valid, float B_scale) {
+    const int t = threadIdx.x;
     const int s = t >> 3;  // sample of this thread for the per-sample passes
     const int g = t & 7;   // its slice of units: g, g + 8, ..., g + 56
     // layer 1
@@ -154,16 +163,31 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
         S.h1t[s][u] = bf(h);
     }
     __syncthreads();
-    // layer 2
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int v = g + 8 * i;
-        float acc = 0.0f;
+    // layer 2: thread = 2 samples x 4 units, operands read once per 8 FMAs
+    {
+        const int v0 = 4 * (t & 15), s0 = 2 * (t >> 4);
+        float acc[2][4] = {};
 #pragma unroll 8
-        for (int u = 0; u < H; ++u) acc = fmaf(S.h1t[s][u], S.w2t[u][v], acc);
-        const float h = fmaxf(acc + S.b2[v], 0.0f);
-        S.h2[s][v] = h;
-        S.h2t[s][v] = bf(h);
+        for (int u = 0; u < H; ++u) {
+            const float a0 = S.h1t[s0][u], a1 = S.h1t[s0 + 1][u];
+            const float4 w = *reinterpret_cast<const float4*>(&S.w2t[u][v0]);
+            acc[0][0] = fmaf(a0, w.x, acc[0][0]);
+            acc[0][1] = fmaf(a0, w.y, acc[0][1]);
+            acc[0][2] = fmaf(a0, w.z, acc[0][2]);
+            acc[0][3] = fmaf(a0, w.w, acc[0][3]);
+            acc[1][0] = fmaf(a1, w.x, acc[1][0]);
+            acc[1][1] = fmaf(a1, w.y, acc[1][1]);
+            acc[1][2] = fmaf(a1, w.z, acc[1][2]);
+            acc[1][3] = fmaf(a1, w.w, acc[1][3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float h = fmaxf(acc[j][i] + S.b2[v0 + i], 0.0f);
+                S.h2[s0 + j][v0 + i] = h;
+                S.h2t[s0 + j][v0 + i] = bf(h);
+            }
     }
     __syncthreads();
     // output and residual (8 threads per sample, lanes 8s'..8s'+7 of a warp)
@@ -175,9 +199,9 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
         part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
         part += __shfl_xor_sync(0xFFFFFFFFu, part, 4);
         if (g == 0) {
-            const bool valid = base + s < B;
+            const bool valid = s < n_valid;
             const float r = valid ? (part + S.b3) - S.ys[s] : 0.0f;
-            S.dy[s] = valid ? 2.0f * r / static_cast<float>(B) : 0.0f;
+            S.dy[s] = valid ? 2.0f * r / B_scale : 0.0f;
             S.ys[s] = r * r;  // reuse: squared residual
         }
     }
@@ -191,35 +215,64 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
         S.dz2t[s][v] = bf(d);
     }
     __syncthreads();
-    // dz1 = (dz2~ W2~) [z1 > 0]
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int u = g + 8 * i;
-        float acc = 0.0f;
+    // dz1 = (dz2~ W2~) [z1 > 0], same blocking
+    {
+        const int u0 = 4 * (t & 15), s0 = 2 * (t >> 4);
+        float acc[2][4] = {};
 #pragma unroll 8
-        for (int v = 0; v < H; ++v) acc = fmaf(S.dz2t[s][v], S.w2[v][u], acc);
-        S.dz1[s][u] = S.h1[s][u] > 0.0f ? acc : 0.0f;
+        for (int v = 0; v < H; ++v) {
+            const float a0 = S.dz2t[s0][v], a1 = S.dz2t[s0 + 1][v];
+            const float4 w = *reinterpret_cast<const float4*>(&S.w2[v][u0]);
+            acc[0][0] = fmaf(a0, w.x, acc[0][0]);
+            acc[0][1] = fmaf(a0, w.y, acc[0][1]);
+            acc[0][2] = fmaf(a0, w.z, acc[0][2]);
+            acc[0][3] = fmaf(a0, w.w, acc[0][3]);
+            acc[1][0] = fmaf(a1, w.x, acc[1][0]);
+            acc[1][1] = fmaf(a1, w.y, acc[1][1]);
+            acc[1][2] = fmaf(a1, w.z, acc[1][2]);
+            acc[1][3] = fmaf(a1, w.w, acc[1][3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                S.dz1[s0 + j][u0 + i] = S.h1[s0 + j][u0 + i] > 0.0f ? acc[j][i] : 0.0f;
     }
     __syncthreads();
+}
 
-    // weight gradients of the tile
-    float* out = partial + static_cast<long long>(blockIdx.x) * P;
-    {
-        const int v = t >> 2;
+// The tile's gradient into out[0 .. P) and its squared-residual sum into
+// *loss; kAcc: add to what is there (every parameter has one owner thread).
+template <bool kAcc>
+__device__ void tile_write(const GradSmem& S, int d_in, float* out, float* loss) {
+    const int t = threadIdx.x;
+    {  // dW2: thread = 4 x 4 block, two float4 loads per 16 FMAs
+        const int v0 = 4 * (t >> 4), u0 = 4 * (t & 15);
+        float acc[4][4] = {};
+#pragma unroll 4
+        for (int q = 0; q < kTile; ++q) {
+            const float4 a = *reinterpret_cast<const float4*>(&S.dz2t[q][v0]);
+            const float4 b = *reinterpret_cast<const float4*>(&S.h1t[q][u0]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int u = (t & 3) + 4 * j;
-            float acc = 0.0f;
-#pragma unroll 8
-            for (int q = 0; q < kTile; ++q) acc = fmaf(S.dz2t[q][v], S.h1t[q][u], acc);
-            out[off_w2(d_in) + v * H + u] = acc;
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float& o = out[off_w2(d_in) + (v0 + i) * H + u0 + j];
+                o = kAcc ? o + acc[i][j] : acc[i][j];
+            }
     }
     for (int i = t; i < H * d_in; i += kGradThreads) {
         const int u = i / d_in, k = i - u * d_in;
         float acc = 0.0f;
         for (int q = 0; q < kTile; ++q) acc = fmaf(bf(S.dz1[q][u]), S.xt[q][k], acc);
-        out[i] = acc;
+        out[i] = kAcc ? out[i] + acc : acc;
     }
     if (t < H) {
         float a3 = 0.0f, a2 = 0.0f, a1 = 0.0f;
@@ -228,9 +281,12 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
             a2 += S.dz2[q][t];
             a1 += S.dz1[q][t];
         }
-        out[off_w3(d_in) + t] = a3;
-        out[off_b2(d_in) + t] = a2;
-        out[off_b1(d_in) + t] = a1;
+        float& o3 = out[off_w3(d_in) + t];
+        float& o2 = out[off_b2(d_in) + t];
+        float& o1 = out[off_b1(d_in) + t];
+        o3 = kAcc ? o3 + a3 : a3;
+        o2 = kAcc ? o2 + a2 : a2;
+        o1 = kAcc ? o1 + a1 : a1;
     }
     if (t == H) {
         float a = 0.0f, l = 0.0f;
@@ -238,9 +294,28 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
             a += S.dy[q];
             l += S.ys[q];
         }
-        out[off_b3(d_in)] = a;
-        partial_loss[blockIdx.x] = l;
+        float& ob = out[off_b3(d_in)];
+        ob = kAcc ? ob + a : a;
+        *loss = kAcc ? *loss + l : l;
     }
+}
+
+// Forward + backward of one tile of kTile samples; partial[blockIdx][p] gets
+// the tile's gradient, partial_loss[blockIdx] its sum of squared residuals.
+__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
+    const float* __restrict__ theta, int d_in, const float* __restrict__ X, long long n_total,
+    const float* __restrict__ Y, SampleMap map, long long B, float* __restrict__ partial,
+    float* __restrict__ partial_loss) {
+    extern __shared__ unsigned char smem_raw[];
+    GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+    const long long base = static_cast<long long>(blockIdx.x) * kTile;
+    const int n_valid = static_cast<int>(min(static_cast<long long>(kTile), B - base));
+    stage_weights(S, theta, d_in);
+    stage_tile(S, d_in, X, n_total, Y, map, base, n_valid);
+    __syncthreads();
+    tile_passes(S, d_in, n_valid, static_cast<float>(B));
+    tile_write<false>(S, d_in, partial + static_cast<long long>(blockIdx.x) * n_params(d_in),
+                      partial_loss + blockIdx.x);
 }
 
 // grad[p] = sum over CTAs of partial[c][p] (fixed order); optionally Adam.
@@ -283,6 +358,107 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
     m[p] = mi;
     v[p] = vi;
     theta[p] = theta[p] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// Whole training run in one launch: a cluster of kTrainCluster CTAs keeps the
+// network in shared memory for all epochs.  Each step, CTA r takes the r-th
+// of kTrainCluster contiguous pieces of the minibatch (in tiles of kTile),
+// accumulates its gradient in shared memory, and after a cluster barrier
+// owns the r-th slice of the parameters: it adds that slice of all CTAs'
+// gradients in rank order (distributed shared memory), applies Adam, and
+// writes the new values into every CTA's copy; a second barrier ends the
+// step.  Same arithmetic as mlp_step (BF16 operands, FP32 sums; only the
+// order of the per-sample sums differs), none of its 2 launches per step.
+// ---------------------------------------------------------------------------
+constexpr int kTrainCluster = 16;  // non-portable cluster size (opt-in attribute)
+
+struct TrainArgs {
+    const float* X;  // standardised features, d_in planes of n_tr
+    const float* Y;
+    long long n_tr, B, steps_per_epoch;
+    int epochs, d_in;
+    const unsigned long long* ab;  // per epoch: the affine order (a, b)
+    const float* bc;               // per step: the bias corrections (1 - beta1^t, 1 - beta2^t)
+    float lr, beta1, beta2, eps;
+    float* theta;   // in: initial parameters; out: trained
+    float* losses;  // per step: mean squared residual of the minibatch
+};
+
+__global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(kGradThreads)
+    mlp_train_kernel(TrainArgs ta) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ unsigned char smem_raw[];
+    GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+    const int d_in = ta.d_in;
+    const int P = static_cast<int>(n_params(d_in));
+    const int P4 = (P + 1 + 3) & ~3;  // parameters + the loss slot, padded
+    float* th = reinterpret_cast<float*>(smem_raw + sizeof(GradSmem));  // FP32 masters [P]
+    float* part = th + P4;                                              // gradient [P] + loss [1]
+    const int slice = (P + kTrainCluster - 1) / kTrainCluster;
+    float* mom = part + P4;  // this CTA's slice of the Adam moments
+    float* vel = mom + slice;
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int t = threadIdx.x;
+    const int p_lo = rank * slice, p_hi = min(P, p_lo + slice);
+
+    for (int i = t; i < P; i += kGradThreads) th[i] = ta.theta[i];
+    for (int i = t; i < slice; i += kGradThreads) {
+        mom[i] = 0.0f;
+        vel[i] = 0.0f;
+    }
+    cluster.sync();
+    long long step = 0;
+    for (int ep = 0; ep < ta.epochs; ++ep) {
+        const SampleMap map{nullptr, ta.ab[2 * ep], ta.ab[2 * ep + 1],
+                            static_cast<unsigned long long>(ta.n_tr), 0};
+        for (long long off = 0; off < ta.n_tr; off += ta.B, ++step) {
+            const long long nb = (off + ta.B <= ta.n_tr) ? ta.B : ta.n_tr - off;
+            const long long chunk = (nb + kTrainCluster - 1) / kTrainCluster;
+            const long long lo = min(nb, rank * chunk), hi = min(nb, lo + chunk);
+            SampleMap m = map;
+            m.off = off;
+            stage_weights(S, th, d_in);
+            for (int i = t; i <= P; i += kGradThreads) part[i] = 0.0f;
+            __syncthreads();
+            for (long long p0 = lo; p0 < hi; p0 += kTile) {
+                const int n_valid = static_cast<int>(min(static_cast<long long>(kTile), hi - p0));
+                stage_tile(S, d_in, ta.X, ta.n_tr, ta.Y, m, p0, n_valid);
+                __syncthreads();
+                tile_passes(S, d_in, n_valid, static_cast<float>(nb));
+                tile_write<true>(S, d_in, part, part + P);
+                __syncthreads();
+            }
+            cluster.sync();  // every CTA's gradient is complete
+            const float bc1 = ta.bc[2 * step], bc2 = ta.bc[2 * step + 1];
+            for (int p = p_lo + t; p < p_hi; p += kGradThreads) {
+                float g = 0.0f;
+                for (int r = 0; r < kTrainCluster; ++r) g += cluster.map_shared_rank(part, r)[p];
+                const int q = p - p_lo;
+                const float mi = ta.beta1 * mom[q] + (1.0f - ta.beta1) * g;
+                const float vi = ta.beta2 * vel[q] + (1.0f - ta.beta2) * g * g;
+                mom[q] = mi;
+                vel[q] = vi;
+                const float nv = th[p] - ta.lr * (mi / bc1) / (sqrtf(vi / bc2) + ta.eps);
+                for (int r = 0; r < kTrainCluster; ++r) cluster.map_shared_rank(th, r)[p] = nv;
+            }
+            if (rank == 0 && t == 0) {
+                float l = 0.0f;
+                for (int r = 0; r < kTrainCluster; ++r) l += cluster.map_shared_rank(part, r)[P];
+                ta.losses[step] = l / static_cast<float>(nb);
+            }
+            cluster.sync();  // new parameters everywhere, gradients free
+        }
+    }
+    for (int p = p_lo + t; p < p_hi; p += kGradThreads) ta.theta[p] = th[p];
+}
+
+size_t mlp_train_smem(int d_in) {
+    const int P = static_cast<int>(n_params(d_in));
+    const int P4 = (P + 1 + 3) & ~3;
+    const int slice = (P + kTrainCluster - 1) / kTrainCluster;
+    return sizeof(GradSmem) + (2 * static_cast<size_t>(P4) + 2 * slice) * sizeof(float);
 }
 
 // Inference, one sample per thread, weights (BF16-rounded) in shared memory.
@@ -443,6 +619,22 @@ mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long 
             partial, part_loss, n_cta, P, B, grad, loss, nullptr, nullptr, nullptr, 0, 0, 0, 0, 1, 1);
     }
     return launch_status("mlp reduce");
+}
+
+// All epochs of Adam training in one cluster launch (mlp_train_kernel).
+mrip_status mlp_train(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
+                      const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
+                      float eps, float* theta, float* losses, cudaStream_t st) {
+    if (n_tr == 0 || epochs == 0) return MRIP_OK;
+    const size_t smem = mlp_train_smem(d_in);
+    cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return cuda_status(e, "mlp train: kernel attributes");
+    TrainArgs ta{X, Y, n_tr, B, (n_tr + B - 1) / B, epochs, d_in, d_ab, d_bc, lr, beta1, beta2, eps, theta,
+                 losses};
+    mlp_train_kernel<<<kTrainCluster, kGradThreads, smem, st>>>(ta);
+    return launch_status("mlp train");
 }
 
 mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat, cudaStream_t st) {
