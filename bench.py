@@ -633,16 +633,25 @@ def _median_hw(stats):
     return float(np.median([s["half_width"] for s in stats]))
 
 
-def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10):
-    """Tandem workload (4,096 design points x 10,000 clients): the target is
-    the median plain 95 % half-width at n_reps replications.  The plain
-    estimator reaches it by definition in the time of that run; the
-    control-variate estimator is run at n_reps, its replication count is
-    scaled by (half-width ratio)^2 to the target, and it is run again at that
-    count, timed end to end (simulation, training, control runs, inference,
+def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10, which="tandem_cv"):
+    """Tandem workload (4,096 design points x 10,000 clients) or the 256x256
+    forest fire (64 design points x 2,000 steps): the target is the median
+    plain 95 % half-width at n_reps replications.  The plain estimator
+    reaches it by definition in the time of that run; the control-variate
+    estimator is run at n_reps, its replication count is scaled by
+    (half-width ratio)^2 to the target, and it is run again at that count,
+    timed end to end (simulation, training, control runs, inference,
     estimator)."""
-    w = mrip_inputs.workload("tandem_cv")
-    model = eng.Model(eng.MRIP_TANDEM3, n_clients=w["n_clients"], window=w["window"])
+    w = mrip_inputs.workload(which)
+    if which == "tandem_cv":
+        model = eng.Model(eng.MRIP_TANDEM3, n_clients=w["n_clients"], window=w["window"])
+        label = ("tandem_cv: 3-station tandem, 4096 design points, 10000 clients, network 8-64-64-1 "
+                 "on 10 percent of replications, {} control runs per held-out replication").format(m_factor)
+    else:
+        model = eng.Model(eng.MRIP_FOREST_FIRE, L=w["L"], n_steps=w["n_steps"], density=w["density"],
+                          window=w["window"])
+        label = ("ff256_cv: forest fire 256x256, 64 design points, 2000 steps, network 6-64-64-1 on "
+                 "10 percent of replications, {} control runs per held-out replication").format(m_factor)
     model.set_stream(stream)
 
     def timed(fn):
@@ -669,14 +678,12 @@ def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10):
                                              / (1 - CV_DEFAULTS["train_frac"]))))
     (pl2, cv2, loss2), t_cv = timed(lambda: cv_run(n_need))
     # held-out plain half-width at equal replications (what the network buys)
-    y = model.outputs(0).reshape(w["n_dp"], n_need)
+    y = model.outputs(0 if which == "tandem_cv" else 1).reshape(w["n_dp"], n_need)  # per-replication Y
     n_tr = math.ceil(CV_DEFAULTS["train_frac"] * n_need)
     ratio = [c["half_width"] / (np.std(y[d, n_tr:], ddof=1) / math.sqrt(n_need - n_tr)
                                 * c["t_crit"]) for d, c in enumerate(cv2)]
     model.close()
-    return {"workload": ("tandem_cv: 3-station tandem, 4096 design points, 10000 clients, "
-                         "network 8-64-64-1 on 10 percent of replications, "
-                         "{} control runs per held-out replication").format(m_factor),
+    return {"workload": label,
             "target_half_width": target,
             "plain": {"replications": n_reps, "seconds": t_plain,
                       "median_half_width": target},
@@ -1001,7 +1008,11 @@ def main():
     if extra:
         line["rates"] = extra
     if rank == 0 and world == 1 and not args.no_cv:
-        line["time_to_target"] = time_to_target(eng, torch, stream, 42)
+        if args.workload in ("ff256", "ff256_skip"):
+            line["time_to_target"] = time_to_target(eng, torch, stream, 42, n_reps=128, m_factor=2,
+                                                    which="ff256_cv")
+        else:
+            line["time_to_target"] = time_to_target(eng, torch, stream, 42)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = oracle.host_threads()
