@@ -900,12 +900,17 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
     } else if (mapping == MRIP_MAP_CTA) {
         if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_mm1_simulate: too many replications for CTA");
         // about 4 clients per thread, 32 .. 1024 threads; fixed-point variates
-        // staged in shared memory between the passes when they fit 48 KiB
+        // staged in shared memory between the passes when they fit 96 KiB
         long long threads = ((n_clients + 3) / 4 + 31) / 32 * 32;
         threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
         const long long per_thread = (n_clients + threads - 1) / threads;
         const size_t stage = static_cast<size_t>(threads * per_thread) * 2 * sizeof(long long);
-        const bool staged = stage <= 48 * 1024;
+        const bool staged = stage <= 96 * 1024;  // plus ~3.3 KB of static shared memory
+        if (staged && stage > 40 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(mm1_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 96 * 1024);
+            if (e != cudaSuccess) return cuda_status(e, "mrip_mm1_simulate: shared memory attribute");
+        }
         mm1_cta_kernel<<<static_cast<unsigned>(n_items), static_cast<unsigned>(threads), staged ? stage : 0, st>>>(
             d_dps, n_reps, n_clients, staged, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_COOP) {
