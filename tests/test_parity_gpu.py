@@ -638,3 +638,28 @@ def test_forest_fire_skip_workload_full_sampled(eng, torch_mod):
             assert np.array_equal(gc[pick[k]], rc[k])
     assert np.count_nonzero(ties == 0) >= 3
     assert gc.min() >= 0 and gc.max() <= w["L"] ** 2
+
+
+# ------------------------------------------------------------------ empty batches
+def test_every_stage_accepts_an_empty_batch(eng, torch_mod):
+    """Zero replications (or design points) is a valid request for every stage
+    entry point: it succeeds and leaves the outputs untouched."""
+    t = torch_mod
+    sentinel = t.full((4,), 7.0, dtype=t.float64, device="cuda")
+    eng.mrip_mm1_simulate(dev(t, MM1_DPS), 0, 100, 42, eng.MRIP_MAP_CTA, sentinel)
+    eng.mrip_mm1_simulate(dev(t, MM1_DPS), 0, 100, 42, eng.MRIP_MAP_THREAD, sentinel)
+    eng.mrip_tandem3_simulate(dev(t, mrip_inputs.tandem_design_points(2, seed=1)), 0, 0, 100, 10, 42,
+                              0, eng.MRIP_MAP_WARP_COOP, sentinel)
+    counts = t.full((4,), 7, dtype=t.int32, device="cuda")
+    eng.mrip_forest_fire_simulate(dev(t, [[0.01, 1e-5]]), 0, 64, 10, 0.5, 42, None, counts)
+    eng.mrip_forest_fire_skip_simulate(dev(t, [[0.01, 1e-5]]), 0, 64, 10, 0.5, 42, None, counts)
+    tau = t.full((4,), 7, dtype=t.int64, device="cuda")
+    eng.mrip_walk_simulate(np.array([16.0]), 0, 42, 1 << 20, eng.MRIP_MAP_PERSISTENT, tau)
+    eng.mrip_pi_simulate(0, 1000, 42, tau)
+    fa = t.full((4,), 7, dtype=t.int32, device="cuda")
+    eng.mrip_area_walk_simulate(0, 100, 42, eng.MRIP_MAP_THREAD, fa, None)
+    eng.mrip_stats_reduce(t.empty((0, 5), dtype=t.float64, device="cuda"), sentinel)
+    t.cuda.synchronize()
+    assert sentinel.cpu().tolist() == [7.0] * 4
+    assert counts.cpu().tolist() == [7] * 4 and tau.cpu().tolist() == [7] * 4
+    assert fa.cpu().tolist() == [7] * 4
