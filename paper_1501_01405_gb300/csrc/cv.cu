@@ -214,7 +214,7 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     if (e != cudaSuccess) return cuda_status(e, "cv: training schedule");
     s = mlp_init(d_in, p->net_seed, theta.as<float>(), st);
     if (s != MRIP_OK) return s;
-    s = mlp_train(d_in, xs_tr.as<float>(), ys_tr.as<float>(), n_tr, B, p->epochs, sched.as<unsigned long long>(),
+    s = mlp_train_tc(d_in, xs_tr.as<float>(), ys_tr.as<float>(), n_tr, B, p->epochs, sched.as<unsigned long long>(),
                   reinterpret_cast<const float*>(static_cast<char*>(sched.p) + ab_bytes), p->lr, p->beta1,
                   p->beta2, p->eps, theta.as<float>(), losses.as<float>(), st);
     if (s != MRIP_OK) return s;

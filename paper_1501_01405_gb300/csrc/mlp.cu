@@ -16,7 +16,9 @@
 // shared memory (both orientations of W2, so every inner product reads
 // consecutive words), and writes its per-parameter partial sums; a second
 // kernel adds the partials of all CTAs in a fixed order (deterministic) and,
-// during training, applies Adam in the same pass.
+// during training, applies Adam in the same pass.  These serve the stage
+// entry points; the control-variate driver trains in one launch on the
+// tensor cores (mlp_train_tc_kernel).
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
@@ -24,6 +26,7 @@
 
 #include "common.cuh"
 #include "model.cuh"
+#include "tc.cuh"
 
 namespace mrip {
 
@@ -42,6 +45,9 @@ __host__ __device__ constexpr long long off_b3(int d) { return off_w3(d) + H; }
 __host__ __device__ constexpr long long n_params(int d) { return off_b3(d) + 1; }
 
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// W1 element (unit u, input k); W1 is stored row-major [u][k].
+__device__ __forceinline__ float theta_w1(const float* theta, int d_in, int u, int k) { return theta[u * d_in + k]; }
 
 // He-uniform weights from stream tag 3: element e of (W1, W2, W3) reads words
 // 2(e mod 2), 2(e mod 2)+1 of block (c0 = e div 2, c1 = 0, rep 0, dp 0).
@@ -242,8 +248,7 @@ __device__ void tile_passes(GradSmem& S, int d_in, int n_valid, float B_scale) {
 }
 
 // The tile's gradient into out[0 .. P) and its squared-residual sum into
-// *loss; kAcc: add to what is there (every parameter has one owner thread).
-template <bool kAcc>
+// *loss (every parameter has one owner thread).
 __device__ void tile_write(const GradSmem& S, int d_in, float* out, float* loss) {
     const int t = threadIdx.x;
     {  // dW2: thread = 4 x 4 block, two float4 loads per 16 FMAs
@@ -264,15 +269,14 @@ __device__ void tile_write(const GradSmem& S, int d_in, float* out, float* loss)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float& o = out[off_w2(d_in) + (v0 + i) * H + u0 + j];
-                o = kAcc ? o + acc[i][j] : acc[i][j];
+                out[off_w2(d_in) + (v0 + i) * H + u0 + j] = acc[i][j];
             }
     }
     for (int i = t; i < H * d_in; i += kGradThreads) {
         const int u = i / d_in, k = i - u * d_in;
         float acc = 0.0f;
         for (int q = 0; q < kTile; ++q) acc = fmaf(bf(S.dz1[q][u]), S.xt[q][k], acc);
-        out[i] = kAcc ? out[i] + acc : acc;
+        out[i] = acc;
     }
     if (t < H) {
         float a3 = 0.0f, a2 = 0.0f, a1 = 0.0f;
@@ -281,12 +285,9 @@ __device__ void tile_write(const GradSmem& S, int d_in, float* out, float* loss)
             a2 += S.dz2[q][t];
             a1 += S.dz1[q][t];
         }
-        float& o3 = out[off_w3(d_in) + t];
-        float& o2 = out[off_b2(d_in) + t];
-        float& o1 = out[off_b1(d_in) + t];
-        o3 = kAcc ? o3 + a3 : a3;
-        o2 = kAcc ? o2 + a2 : a2;
-        o1 = kAcc ? o1 + a1 : a1;
+        out[off_w3(d_in) + t] = a3;
+        out[off_b2(d_in) + t] = a2;
+        out[off_b1(d_in) + t] = a1;
     }
     if (t == H) {
         float a = 0.0f, l = 0.0f;
@@ -294,9 +295,8 @@ __device__ void tile_write(const GradSmem& S, int d_in, float* out, float* loss)
             a += S.dy[q];
             l += S.ys[q];
         }
-        float& ob = out[off_b3(d_in)];
-        ob = kAcc ? ob + a : a;
-        *loss = kAcc ? *loss + l : l;
+        out[off_b3(d_in)] = a;
+        *loss = l;
     }
 }
 
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(
     stage_tile(S, d_in, X, n_total, Y, map, base, n_valid);
     __syncthreads();
     tile_passes(S, d_in, n_valid, static_cast<float>(B));
-    tile_write<false>(S, d_in, partial + static_cast<long long>(blockIdx.x) * n_params(d_in),
+    tile_write(S, d_in, partial + static_cast<long long>(blockIdx.x) * n_params(d_in),
                       partial_loss + blockIdx.x);
 }
 
@@ -361,18 +361,9 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
 }
 
 // ---------------------------------------------------------------------------
-// Whole training run in one launch: a cluster of kTrainCluster CTAs keeps the
-// network in shared memory for all epochs.  Each step, CTA r takes the r-th
-// of kTrainCluster contiguous pieces of the minibatch (in tiles of kTile),
-// accumulates its gradient in shared memory, and after a cluster barrier
-// owns the r-th slice of the parameters: it adds that slice of all CTAs'
-// gradients in rank order (distributed shared memory), applies Adam, and
-// writes the new values into every CTA's copy; a second barrier ends the
-// step.  Same arithmetic as mlp_step (BF16 operands, FP32 sums; only the
-// order of the per-sample sums differs), none of its 2 launches per step.
+// Whole training run in one launch (mlp_train_tc_kernel below): a cluster of
+// CTAs keeps the network in shared memory for all epochs.
 // ---------------------------------------------------------------------------
-constexpr int kTrainCluster = 16;  // non-portable cluster size (opt-in attribute)
-
 struct TrainArgs {
     const float* X;  // standardised features, d_in planes of n_tr
     const float* Y;
@@ -385,80 +376,321 @@ struct TrainArgs {
     float* losses;  // per step: mean squared residual of the minibatch
 };
 
-__global__ void __cluster_dims__(kTrainCluster, 1, 1) __launch_bounds__(kGradThreads)
-    mlp_train_kernel(TrainArgs ta) {
+// ---------------------------------------------------------------------------
+// Training with the four 64-wide contractions on the tensor cores (tcgen05,
+// FP32 accumulators in tensor memory).  A cluster of kTcCluster CTAs of 128
+// threads holds the FP32 parameters in every CTA's shared memory; per step
+// each CTA takes 1/kTcCluster of the minibatch in tiles of 128 samples
+// (thread m = sample m = TMEM lane m):
+//   Z1  = X~ W1~^T        (M 128, N 64, K 16: the d_in features, zero-padded)
+//   Z2  = H1~ W2~^T       (K 64)
+//   dH1 = dZ2~ W2~        (K 64, B = W2~ transposed)
+//   dW2 = dZ2~^T H1~      (M 128 with rows 64..127 zero, K = the 128 samples)
+// Each thread turns its row of Z1 / Z2 / dH1 into activations, residual and
+// deltas (FP32, rounded to BF16 where the next contraction reads them) and
+// writes them in the operands' core-matrix layouts; the bias, W3 and W1
+// gradients are FP32 column sums over the tile in sample order, as in the
+// SIMT kernels.  After a cluster barrier CTA r owns the r-th slice of the
+// parameters: it adds that slice of every CTA's gradient in rank order over
+// distributed shared memory, applies Adam and writes the new values into
+// every CTA's copy; a second barrier ends the step.  Same arithmetic as
+// mlp_step (BF16 operands, FP32 sums; only the order of the sums differs).
+// Every MMA completion is awaited with an
+// iteration limit; on a timeout the CTA stops issuing MMAs, runs on to the
+// same barriers (so no peer waits forever) and reports it in *err.
+// ---------------------------------------------------------------------------
+constexpr int kTcCluster = 8;
+constexpr int kTcThreads = 128;
+constexpr int kTcRows = 128;
+constexpr int kTcWait = 1 << 22;
+
+struct TcSmem {
+    alignas(1024) unsigned char a1[kTcRows * 16 * 2];      // X~ tile, K = 16
+    alignas(1024) unsigned char w1b[H * 16 * 2];           // W1~ as B, K = 16
+    alignas(1024) unsigned char a2[kTcRows * H * 2];       // H1~ rows, K = 64
+    alignas(1024) unsigned char w2b[H * H * 2];            // W2~ [v][u] as B
+    alignas(1024) unsigned char w2tb[H * H * 2];           // W2~ [u][v] as B
+    alignas(1024) unsigned char h1tt[H * kTcRows * 2];     // H1~ transposed [u][m], K = 128
+    alignas(1024) unsigned char a3[kTcRows * H * 2];       // dZ2~ rows, K = 64
+    alignas(1024) unsigned char dz2tt[kTcRows * kTcRows * 2];  // dZ2~ transposed [v][m]; rows 64.. zero
+    float f32[kTcRows][H + 1];                             // dZ2, then dZ1 (FP32)
+    __nv_bfloat16 h2t[kTcRows][H + 2];                     // H2~ rows (for dW3)
+    float xs[kTcRows][kMaxIn + 1];                         // X~ (for dW1)
+    float dy[kTcRows], r2[kTcRows];
+    float w3[H], b1[H], b2[H];
+    float b3;
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ void put_bf16(unsigned char* tile, uint32_t off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(tile + off) = __float2bfloat16_rn(v);
+}
+
+__global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
+    mlp_train_tc_kernel(TrainArgs ta, int* err) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ unsigned char smem_raw[];
-    GradSmem& S = *reinterpret_cast<GradSmem*>(smem_raw);
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw);
     const int d_in = ta.d_in;
     const int P = static_cast<int>(n_params(d_in));
-    const int P4 = (P + 1 + 3) & ~3;  // parameters + the loss slot, padded
-    float* th = reinterpret_cast<float*>(smem_raw + sizeof(GradSmem));  // FP32 masters [P]
-    float* part = th + P4;                                              // gradient [P] + loss [1]
-    const int slice = (P + kTrainCluster - 1) / kTrainCluster;
-    float* mom = part + P4;  // this CTA's slice of the Adam moments
+    const int P4 = (P + 1 + 3) & ~3;
+    float* th = reinterpret_cast<float*>(tc_raw + sizeof(TcSmem));
+    float* part = th + P4;
+    const int slice = (P + kTcCluster - 1) / kTcCluster;
+    float* mom = part + P4;
     float* vel = mom + slice;
     const int rank = static_cast<int>(cluster.block_rank());
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5;
     const int p_lo = rank * slice, p_hi = min(P, p_lo + slice);
+    constexpr uint32_t kIdesc = tc::idesc_bf16(kTcRows, H);
 
-    for (int i = t; i < P; i += kGradThreads) th[i] = ta.theta[i];
-    for (int i = t; i < slice; i += kGradThreads) {
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
+    if (t == 0) tc::mbar_init(&S.bar);
+    for (int i = t; i < P; i += kTcThreads) th[i] = ta.theta[i];
+    for (int i = t; i < slice; i += kTcThreads) {
         mom[i] = 0.0f;
         vel[i] = 0.0f;
     }
+    for (int i = t; i < kTcRows * kTcRows * 2 / 16; i += kTcThreads)
+        reinterpret_cast<uint4*>(S.dz2tt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < kTcRows * 16 * 2 / 16; i += kTcThreads)
+        reinterpret_cast<uint4*>(S.a1)[i] = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_before_sync();
     cluster.sync();
+    tc::fence_after_sync();
+    const uint32_t tm = S.tmem;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // one MMA group's completion: every thread polls; ok stays CTA-uniform
+    auto wait_mma = [&]() {
+        bool mine = ok ? tc::mbar_wait(&S.bar, phase, kTcWait) : false;
+        phase ^= 1u;
+        tc::fence_before_sync();
+        const bool all = __syncthreads_and(mine) != 0;
+        tc::fence_after_sync();
+        if (ok && !all) {
+            ok = false;
+            if (t == 0) atomicExch(err, 1);
+        }
+    };
+
     long long step = 0;
     for (int ep = 0; ep < ta.epochs; ++ep) {
-        const SampleMap map{nullptr, ta.ab[2 * ep], ta.ab[2 * ep + 1],
-                            static_cast<unsigned long long>(ta.n_tr), 0};
+        const SampleMap map{nullptr, ta.ab[2 * ep], ta.ab[2 * ep + 1], static_cast<unsigned long long>(ta.n_tr), 0};
         for (long long off = 0; off < ta.n_tr; off += ta.B, ++step) {
             const long long nb = (off + ta.B <= ta.n_tr) ? ta.B : ta.n_tr - off;
-            const long long chunk = (nb + kTrainCluster - 1) / kTrainCluster;
+            const long long chunk = (nb + kTcCluster - 1) / kTcCluster;
             const long long lo = min(nb, rank * chunk), hi = min(nb, lo + chunk);
-            SampleMap m = map;
-            m.off = off;
-            stage_weights(S, th, d_in);
-            for (int i = t; i <= P; i += kGradThreads) part[i] = 0.0f;
-            __syncthreads();
-            for (long long p0 = lo; p0 < hi; p0 += kTile) {
-                const int n_valid = static_cast<int>(min(static_cast<long long>(kTile), hi - p0));
-                stage_tile(S, d_in, ta.X, ta.n_tr, ta.Y, m, p0, n_valid);
+            SampleMap smap = map;
+            smap.off = off;
+            // BF16 operands of this step's weights
+            for (int i = t; i < H * 16; i += kTcThreads) {
+                const int u = i >> 4, k = i & 15;
+                put_bf16(S.w1b, tc::core_offset(u, k, 16), k < d_in ? theta_w1(th, d_in, u, k) : 0.0f);
+            }
+            for (int i = t; i < H * H; i += kTcThreads) {
+                const int v = i / H, u = i - v * H;
+                const float w = th[off_w2(d_in) + i];
+                put_bf16(S.w2b, tc::core_offset(v, u, H), w);
+                put_bf16(S.w2tb, tc::core_offset(u, v, H), w);
+            }
+            for (int i = t; i < H; i += kTcThreads) {
+                S.w3[i] = bf(th[off_w3(d_in) + i]);
+                S.b1[i] = th[off_b1(d_in) + i];
+                S.b2[i] = th[off_b2(d_in) + i];
+            }
+            if (t == 0) S.b3 = th[off_b3(d_in)];
+            for (int i = t; i <= P; i += kTcThreads) part[i] = 0.0f;
+
+            for (long long p0 = lo; p0 < hi; p0 += kTcRows) {
+                const int n_valid = static_cast<int>(min(static_cast<long long>(kTcRows), hi - p0));
+                const int m = t;  // this thread's sample / TMEM lane
+                const bool valid = m < n_valid;
+                float y = 0.0f;
+                {
+                    const long long smp = valid ? sample_of(smap, p0 + m) : 0;
+                    for (int k = 0; k < kMaxIn; ++k) {
+                        const float x = (valid && k < d_in) ? bf(ta.X[k * ta.n_tr + smp]) : 0.0f;
+                        S.xs[m][k] = x;
+                        if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
+                    }
+                    if (valid) y = ta.Y[smp];
+                }
+                tc::fence_smem_async();
+                tc::fence_before_sync();
                 __syncthreads();
-                tile_passes(S, d_in, n_valid, static_cast<float>(nb));
-                tile_write<true>(S, d_in, part, part + P);
+                tc::fence_after_sync();
+                if (t == 0 && ok) {
+                    tc::mma_bf16(tm, tc::smem_desc(tc::smem_addr(S.a1), 128, 256),
+                                 tc::smem_desc(tc::smem_addr(S.w1b), 128, 256), kIdesc, false);
+                    tc::mma_commit(&S.bar);
+                }
+                wait_mma();
+                // layer 1 epilogue: h1 = relu(z1 + b1)
+                uint32_t mask1[2] = {0u, 0u};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float z[16];
+                    tc::tmem_ld16(tm + lane_base + 16 * c, z);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int u = 16 * c + j;
+                        const float h = fmaxf(z[j] + S.b1[u], 0.0f);
+                        if (h > 0.0f) mask1[u >> 5] |= 1u << (u & 31);
+                        const float hb = bf(h);
+                        put_bf16(S.a2, tc::core_offset(m, u, H), hb);
+                        put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), hb);
+                    }
+                }
+                tc::fence_smem_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (t == 0 && ok) {
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        tc::mma_bf16(tm + 64, tc::smem_desc(tc::smem_addr(S.a2) + 256 * ks, 128, 1024),
+                                     tc::smem_desc(tc::smem_addr(S.w2b) + 256 * ks, 128, 1024), kIdesc, ks > 0);
+                    tc::mma_commit(&S.bar);
+                }
+                wait_mma();
+                // layer 2 epilogue: h2, output, residual, dZ2
+                float yhat = 0.0f;
+                uint32_t mask2[2] = {0u, 0u};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float z[16];
+                    tc::tmem_ld16(tm + lane_base + 64 + 16 * c, z);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int v = 16 * c + j;
+                        const float h = fmaxf(z[j] + S.b2[v], 0.0f);
+                        if (h > 0.0f) mask2[v >> 5] |= 1u << (v & 31);
+                        const float hb = bf(h);
+                        S.h2t[m][v] = __float2bfloat16_rn(hb);
+                        yhat = fmaf(hb, S.w3[v], yhat);
+                    }
+                }
+                const float r = valid ? (yhat + S.b3) - y : 0.0f;
+                const float dyv = valid ? 2.0f * r / static_cast<float>(nb) : 0.0f;
+                S.dy[m] = dyv;
+                S.r2[m] = r * r;
+#pragma unroll 8
+                for (int v = 0; v < H; ++v) {
+                    const float d = ((mask2[v >> 5] >> (v & 31)) & 1u) ? dyv * S.w3[v] : 0.0f;
+                    S.f32[m][v] = d;
+                    const float db = bf(d);
+                    put_bf16(S.a3, tc::core_offset(m, v, H), db);
+                    put_bf16(S.dz2tt, tc::core_offset(v, m, kTcRows), db);
+                }
+                tc::fence_smem_async();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (t == 0 && ok) {
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)  // dH1 = dZ2~ W2~
+                        tc::mma_bf16(tm, tc::smem_desc(tc::smem_addr(S.a3) + 256 * ks, 128, 1024),
+                                     tc::smem_desc(tc::smem_addr(S.w2tb) + 256 * ks, 128, 1024), kIdesc, ks > 0);
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks)  // dW2 = dZ2~^T H1~
+                        tc::mma_bf16(tm + 128, tc::smem_desc(tc::smem_addr(S.dz2tt) + 256 * ks, 128, 2048),
+                                     tc::smem_desc(tc::smem_addr(S.h1tt) + 256 * ks, 128, 2048), kIdesc, ks > 0);
+                    tc::mma_commit(&S.bar);
+                }
+                // meanwhile: column sums of this tile's dZ2 (b2), dy h2~ (W3), dy (b3), r^2
+                if (t < H) {
+                    float a2 = 0.0f, a3 = 0.0f;
+                    for (int q = 0; q < kTcRows; ++q) {
+                        a2 += S.f32[q][t];
+                        a3 = fmaf(S.dy[q], __bfloat162float(S.h2t[q][t]), a3);
+                    }
+                    part[off_b2(d_in) + t] += a2;
+                    part[off_w3(d_in) + t] += a3;
+                } else if (t == H) {
+                    float a = 0.0f, l = 0.0f;
+                    for (int q = 0; q < kTcRows; ++q) {
+                        a += S.dy[q];
+                        l += S.r2[q];
+                    }
+                    part[off_b3(d_in)] += a;
+                    part[P] += l;
+                }
+                wait_mma();  // includes the barrier that frees S.f32
+                // dZ1 = dH1 [z1 > 0]; dW2 rows 0..63 into the gradient
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float z[16];
+                    tc::tmem_ld16(tm + lane_base + 16 * c, z);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int u = 16 * c + j;
+                        S.f32[m][u] = ((mask1[u >> 5] >> (u & 31)) & 1u) ? z[j] : 0.0f;
+                    }
+                }
+                if (warp < 2) {  // TMEM lanes 0..63 hold dW2 rows v = m
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float z[16];
+                        tc::tmem_ld16(tm + lane_base + 128 + 16 * c, z);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) part[off_w2(d_in) + m * H + 16 * c + j] += z[j];
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                // column sums of dZ1: b1 and W1 (with BF16-rounded dZ1)
+                if (t < H) {
+                    float a1 = 0.0f;
+                    for (int q = 0; q < kTcRows; ++q) a1 += S.f32[q][t];
+                    part[off_b1(d_in) + t] += a1;
+                }
+                for (int i = t; i < H * d_in; i += kTcThreads) {
+                    const int u = i / d_in, k = i - u * d_in;
+                    float acc = 0.0f;
+                    for (int q = 0; q < kTcRows; ++q) acc = fmaf(bf(S.f32[q][u]), S.xs[q][k], acc);
+                    part[i] += acc;
+                }
                 __syncthreads();
             }
             cluster.sync();  // every CTA's gradient is complete
             const float bc1 = ta.bc[2 * step], bc2 = ta.bc[2 * step + 1];
-            for (int p = p_lo + t; p < p_hi; p += kGradThreads) {
+            for (int p = p_lo + t; p < p_hi; p += kTcThreads) {
                 float g = 0.0f;
-                for (int r = 0; r < kTrainCluster; ++r) g += cluster.map_shared_rank(part, r)[p];
+                for (int rr = 0; rr < kTcCluster; ++rr) g += cluster.map_shared_rank(part, rr)[p];
                 const int q = p - p_lo;
                 const float mi = ta.beta1 * mom[q] + (1.0f - ta.beta1) * g;
                 const float vi = ta.beta2 * vel[q] + (1.0f - ta.beta2) * g * g;
                 mom[q] = mi;
                 vel[q] = vi;
                 const float nv = th[p] - ta.lr * (mi / bc1) / (sqrtf(vi / bc2) + ta.eps);
-                for (int r = 0; r < kTrainCluster; ++r) cluster.map_shared_rank(th, r)[p] = nv;
+                for (int rr = 0; rr < kTcCluster; ++rr) cluster.map_shared_rank(th, rr)[p] = nv;
             }
             if (rank == 0 && t == 0) {
                 float l = 0.0f;
-                for (int r = 0; r < kTrainCluster; ++r) l += cluster.map_shared_rank(part, r)[P];
+                for (int rr = 0; rr < kTcCluster; ++rr) l += cluster.map_shared_rank(part, rr)[P];
                 ta.losses[step] = l / static_cast<float>(nb);
             }
-            cluster.sync();  // new parameters everywhere, gradients free
+            cluster.sync();
         }
     }
-    for (int p = p_lo + t; p < p_hi; p += kGradThreads) ta.theta[p] = th[p];
+    for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta[p] = th[p];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_free(tm, 256);
 }
 
-size_t mlp_train_smem(int d_in) {
+size_t mlp_train_tc_smem(int d_in) {
     const int P = static_cast<int>(n_params(d_in));
     const int P4 = (P + 1 + 3) & ~3;
-    const int slice = (P + kTrainCluster - 1) / kTrainCluster;
-    return sizeof(GradSmem) + (2 * static_cast<size_t>(P4) + 2 * slice) * sizeof(float);
+    const int slice = (P + kTcCluster - 1) / kTcCluster;
+    return sizeof(TcSmem) + (2 * static_cast<size_t>(P4) + 2 * slice) * sizeof(float);
 }
 
 // Inference, one sample per thread, weights (BF16-rounded) in shared memory.
@@ -621,20 +853,34 @@ mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long 
     return launch_status("mlp reduce");
 }
 
-// All epochs of Adam training in one cluster launch (mlp_train_kernel).
-mrip_status mlp_train(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
-                      const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
-                      float eps, float* theta, float* losses, cudaStream_t st) {
+__device__ int g_tc_timeout;
+
+// All epochs of Adam training in one cluster launch with the contractions on
+// the tensor cores (mlp_train_tc_kernel).  Synchronous: reads back whether an
+// MMA completion wait ran out.
+mrip_status mlp_train_tc(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
+                         const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
+                         float eps, float* theta, float* losses, cudaStream_t st) {
     if (n_tr == 0 || epochs == 0) return MRIP_OK;
-    const size_t smem = mlp_train_smem(d_in);
-    cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = mlp_train_tc_smem(d_in);
+    cudaError_t e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return cuda_status(e, "mlp train: kernel attributes");
+    if (e != cudaSuccess) return cuda_status(e, "mlp train: shared memory attribute");
+    int* flag = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_tc_timeout);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_status(e, "mlp train: timeout flag");
     TrainArgs ta{X, Y, n_tr, B, (n_tr + B - 1) / B, epochs, d_in, d_ab, d_bc, lr, beta1, beta2, eps, theta,
                  losses};
-    mlp_train_kernel<<<kTrainCluster, kGradThreads, smem, st>>>(ta);
-    return launch_status("mlp train");
+    mlp_train_tc_kernel<<<kTcCluster, kTcThreads, smem, st>>>(ta, flag);
+    mrip_status s = launch_status("mlp train (tensor cores)");
+    if (s != MRIP_OK) return s;
+    int h = 0;
+    e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "mlp train (tensor cores)");
+    if (h) return fail(MRIP_ECUDA, "mlp train: a tensor-core MMA did not complete in time");
+    return MRIP_OK;
 }
 
 mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat, cudaStream_t st) {

@@ -97,9 +97,9 @@ mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long 
                      const int64_t* idx, unsigned long long a, unsigned long long b, unsigned long long n_perm,
                      long long off, long long B, float* partial, float* grad, float* loss, float* theta,
                      float* m, float* v, const float* adam, cudaStream_t st);
-mrip_status mlp_train(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
-                      const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
-                      float eps, float* theta, float* losses, cudaStream_t st);
+mrip_status mlp_train_tc(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
+                         const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
+                         float eps, float* theta, float* losses, cudaStream_t st);
 mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat,
                         cudaStream_t st);
 mrip_status cv_reduce(const double* y, const double* g, long long n, const double* gc, long long m,
