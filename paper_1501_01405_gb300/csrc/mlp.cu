@@ -378,19 +378,19 @@ struct TrainArgs {
 
 // ---------------------------------------------------------------------------
 // Training with the four 64-wide contractions on the tensor cores (tcgen05,
-// FP32 accumulators in tensor memory).  A cluster of kTcCluster CTAs of 128
+// FP32 accumulators in tensor memory).  A cluster of kTcCluster CTAs of 512
 // threads holds the FP32 parameters in every CTA's shared memory; per step
 // each CTA takes 1/kTcCluster of the minibatch in tiles of 128 samples
-// (thread m = sample m = TMEM lane m):
+// (sample m = TMEM lane m, its 64 columns split over 4 threads):
 //   Z1  = X~ W1~^T        (M 128, N 64, K 16: the d_in features, zero-padded)
 //   Z2  = H1~ W2~^T       (K 64)
 //   dH1 = dZ2~ W2~        (K 64, B = W2~ transposed)
 //   dW2 = dZ2~^T H1~      (M 128 with rows 64..127 zero, K = the 128 samples)
-// Each thread turns its row of Z1 / Z2 / dH1 into activations, residual and
-// deltas (FP32, rounded to BF16 where the next contraction reads them) and
-// writes them in the operands' core-matrix layouts; the bias, W3 and W1
-// gradients are FP32 column sums over the tile in sample order, as in the
-// SIMT kernels.  After a cluster barrier CTA r owns the r-th slice of the
+// Each thread turns its 16 columns of a row of Z1 / Z2 / dH1 into
+// activations, residual and deltas (FP32, rounded to BF16 where the next
+// contraction reads them) and writes them in the operands' core-matrix
+// layouts; the bias, W3 and W1 gradients are FP32 column sums over the tile
+// in a fixed order (chunks of 16 samples, then the chunks in order).  After a cluster barrier CTA r owns the r-th slice of the
 // parameters: it adds that slice of every CTA's gradient in rank order over
 // distributed shared memory, applies Adam and writes the new values into
 // every CTA's copy; a second barrier ends the step.  Same arithmetic as
@@ -400,8 +400,9 @@ struct TrainArgs {
 // same barriers (so no peer waits forever) and reports it in *err.
 // ---------------------------------------------------------------------------
 constexpr int kTcCluster = 8;
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;  // 4 threads per sample row, 16 columns each
 constexpr int kTcRows = 128;
+constexpr int kTcChunks = kTcThreads / H;  // row chunks of the column sums
 constexpr int kTcWait = 1 << 22;
 
 struct TcSmem {
@@ -416,6 +417,8 @@ struct TcSmem {
     float f32[kTcRows][H + 1];                             // dZ2, then dZ1 (FP32)
     __nv_bfloat16 h2t[kTcRows][H + 2];                     // H2~ rows (for dW3)
     float xs[kTcRows][kMaxIn + 1];                         // X~ (for dW1)
+    float ypart[4][kTcRows];                               // output partials per column block
+    float colpart[3][kTcChunks][H];                        // column sums per row chunk
     float dy[kTcRows], r2[kTcRows];
     float w3[H], b1[H], b2[H];
     float b3;
@@ -427,7 +430,7 @@ __device__ __forceinline__ void put_bf16(unsigned char* tile, uint32_t off, floa
     *reinterpret_cast<__nv_bfloat16*>(tile + off) = __float2bfloat16_rn(v);
 }
 
-__global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
+__global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads, 1)
     mlp_train_tc_kernel(TrainArgs ta, int* err) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
@@ -442,7 +445,10 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
     float* mom = part + P4;
     float* vel = mom + slice;
     const int rank = static_cast<int>(cluster.block_rank());
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int quarter = warp & 3, cb = warp >> 2;  // TMEM lane quarter, column block
+    const int m = 32 * quarter + lane;              // this thread's sample row / TMEM lane
+    const int c0 = 16 * cb;                         // its 16 columns
     const int p_lo = rank * slice, p_hi = min(P, p_lo + slice);
     constexpr uint32_t kIdesc = tc::idesc_bf16(kTcRows, H);
 
@@ -461,7 +467,7 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
     cluster.sync();
     tc::fence_after_sync();
     const uint32_t tm = S.tmem;
-    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * quarter) << 16;
     uint32_t phase = 0;
     bool ok = true;
 
@@ -476,6 +482,12 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
             ok = false;
             if (t == 0) atomicExch(err, 1);
         }
+    };
+    auto sync_for_mma = [&]() {
+        tc::fence_smem_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
     };
 
     long long step = 0;
@@ -508,48 +520,37 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
 
             for (long long p0 = lo; p0 < hi; p0 += kTcRows) {
                 const int n_valid = static_cast<int>(min(static_cast<long long>(kTcRows), hi - p0));
-                const int m = t;  // this thread's sample / TMEM lane
                 const bool valid = m < n_valid;
-                float y = 0.0f;
-                {
-                    const long long smp = valid ? sample_of(smap, p0 + m) : 0;
-                    for (int k = 0; k < kMaxIn; ++k) {
-                        const float x = (valid && k < d_in) ? bf(ta.X[k * ta.n_tr + smp]) : 0.0f;
-                        S.xs[m][k] = x;
-                        if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
-                    }
-                    if (valid) y = ta.Y[smp];
+                const long long smp = valid ? sample_of(smap, p0 + m) : 0;
+                for (int k = 2 * cb; k < 2 * cb + 2; ++k) {  // features 2cb, 2cb + 1 of row m
+                    const float x = (valid && k < d_in) ? bf(ta.X[k * ta.n_tr + smp]) : 0.0f;
+                    S.xs[m][k] = x;
+                    if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
                 }
-                tc::fence_smem_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
+                const float y = valid ? ta.Y[smp] : 0.0f;
+                sync_for_mma();
                 if (t == 0 && ok) {
                     tc::mma_bf16(tm, tc::smem_desc(tc::smem_addr(S.a1), 128, 256),
                                  tc::smem_desc(tc::smem_addr(S.w1b), 128, 256), kIdesc, false);
                     tc::mma_commit(&S.bar);
                 }
                 wait_mma();
-                // layer 1 epilogue: h1 = relu(z1 + b1)
-                uint32_t mask1[2] = {0u, 0u};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                // layer 1 epilogue: h1 = relu(z1 + b1) on columns c0 .. c0 + 15
+                uint32_t mask1 = 0u;
+                {
                     float z[16];
-                    tc::tmem_ld16(tm + lane_base + 16 * c, z);
+                    tc::tmem_ld16(tm + lane_base + c0, z);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int u = 16 * c + j;
+                        const int u = c0 + j;
                         const float h = fmaxf(z[j] + S.b1[u], 0.0f);
-                        if (h > 0.0f) mask1[u >> 5] |= 1u << (u & 31);
+                        if (h > 0.0f) mask1 |= 1u << j;
                         const float hb = bf(h);
                         put_bf16(S.a2, tc::core_offset(m, u, H), hb);
                         put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), hb);
                     }
                 }
-                tc::fence_smem_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
+                sync_for_mma();
                 if (t == 0 && ok) {
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
@@ -558,39 +559,40 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
                     tc::mma_commit(&S.bar);
                 }
                 wait_mma();
-                // layer 2 epilogue: h2, output, residual, dZ2
-                float yhat = 0.0f;
-                uint32_t mask2[2] = {0u, 0u};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float z[16];
-                    tc::tmem_ld16(tm + lane_base + 64 + 16 * c, z);
+                // layer 2 epilogue: h2 and this block's share of the output
+                uint32_t mask2 = 0u;
+                {
+                    float z[16], yp = 0.0f;
+                    tc::tmem_ld16(tm + lane_base + 64 + c0, z);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int v = 16 * c + j;
+                        const int v = c0 + j;
                         const float h = fmaxf(z[j] + S.b2[v], 0.0f);
-                        if (h > 0.0f) mask2[v >> 5] |= 1u << (v & 31);
+                        if (h > 0.0f) mask2 |= 1u << j;
                         const float hb = bf(h);
                         S.h2t[m][v] = __float2bfloat16_rn(hb);
-                        yhat = fmaf(hb, S.w3[v], yhat);
+                        yp = fmaf(hb, S.w3[v], yp);
                     }
+                    S.ypart[cb][m] = yp;
                 }
+                __syncthreads();
+                const float yhat = ((S.ypart[0][m] + S.ypart[1][m]) + S.ypart[2][m]) + S.ypart[3][m];
                 const float r = valid ? (yhat + S.b3) - y : 0.0f;
                 const float dyv = valid ? 2.0f * r / static_cast<float>(nb) : 0.0f;
-                S.dy[m] = dyv;
-                S.r2[m] = r * r;
-#pragma unroll 8
-                for (int v = 0; v < H; ++v) {
-                    const float d = ((mask2[v >> 5] >> (v & 31)) & 1u) ? dyv * S.w3[v] : 0.0f;
+                if (cb == 0) {
+                    S.dy[m] = dyv;
+                    S.r2[m] = r * r;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int v = c0 + j;
+                    const float d = ((mask2 >> j) & 1u) ? dyv * S.w3[v] : 0.0f;
                     S.f32[m][v] = d;
                     const float db = bf(d);
                     put_bf16(S.a3, tc::core_offset(m, v, H), db);
                     put_bf16(S.dz2tt, tc::core_offset(v, m, kTcRows), db);
                 }
-                tc::fence_smem_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
+                sync_for_mma();
                 if (t == 0 && ok) {
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)  // dH1 = dZ2~ W2~
@@ -602,12 +604,23 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
                                      tc::smem_desc(tc::smem_addr(S.h1tt) + 256 * ks, 128, 2048), kIdesc, ks > 0);
                     tc::mma_commit(&S.bar);
                 }
-                // meanwhile: column sums of this tile's dZ2 (b2), dy h2~ (W3), dy (b3), r^2
+                // meanwhile: column sums of dZ2 (b2) and dy h2~ (W3) per chunk of 16 rows
+                {
+                    const int v = t & (H - 1), ch = t / H;
+                    float a2 = 0.0f, a3 = 0.0f;
+                    for (int q = 16 * ch; q < 16 * ch + 16; ++q) {
+                        a2 += S.f32[q][v];
+                        a3 = fmaf(S.dy[q], __bfloat162float(S.h2t[q][v]), a3);
+                    }
+                    S.colpart[0][ch][v] = a2;
+                    S.colpart[1][ch][v] = a3;
+                }
+                wait_mma();  // includes the barrier that frees S.f32
                 if (t < H) {
                     float a2 = 0.0f, a3 = 0.0f;
-                    for (int q = 0; q < kTcRows; ++q) {
-                        a2 += S.f32[q][t];
-                        a3 = fmaf(S.dy[q], __bfloat162float(S.h2t[q][t]), a3);
+                    for (int ch = 0; ch < kTcChunks; ++ch) {
+                        a2 += S.colpart[0][ch][t];
+                        a3 += S.colpart[1][ch][t];
                     }
                     part[off_b2(d_in) + t] += a2;
                     part[off_w3(d_in) + t] += a3;
@@ -620,41 +633,40 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads)
                     part[off_b3(d_in)] += a;
                     part[P] += l;
                 }
-                wait_mma();  // includes the barrier that frees S.f32
-                // dZ1 = dH1 [z1 > 0]; dW2 rows 0..63 into the gradient
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                // dZ1 = dH1 [z1 > 0]; dW2 rows 0..63 (TMEM lanes 0..63) into the gradient
+                {
                     float z[16];
-                    tc::tmem_ld16(tm + lane_base + 16 * c, z);
+                    tc::tmem_ld16(tm + lane_base + c0, z);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int u = 16 * c + j;
-                        S.f32[m][u] = ((mask1[u >> 5] >> (u & 31)) & 1u) ? z[j] : 0.0f;
-                    }
+                    for (int j = 0; j < 16; ++j) S.f32[m][c0 + j] = ((mask1 >> j) & 1u) ? z[j] : 0.0f;
                 }
-                if (warp < 2) {  // TMEM lanes 0..63 hold dW2 rows v = m
+                if (quarter < 2) {
+                    float z[16];
+                    tc::tmem_ld16(tm + lane_base + 128 + c0, z);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        float z[16];
-                        tc::tmem_ld16(tm + lane_base + 128 + 16 * c, z);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) part[off_w2(d_in) + m * H + 16 * c + j] += z[j];
-                    }
+                    for (int j = 0; j < 16; ++j) part[off_w2(d_in) + m * H + c0 + j] += z[j];
                 }
                 tc::fence_before_sync();
                 __syncthreads();
                 tc::fence_after_sync();
-                // column sums of dZ1: b1 and W1 (with BF16-rounded dZ1)
-                if (t < H) {
+                // column sums of dZ1: b1 per chunk, W1 with BF16-rounded dZ1 (one output per thread)
+                {
+                    const int u = t & (H - 1), ch = t / H;
                     float a1 = 0.0f;
-                    for (int q = 0; q < kTcRows; ++q) a1 += S.f32[q][t];
-                    part[off_b1(d_in) + t] += a1;
+                    for (int q = 16 * ch; q < 16 * ch + 16; ++q) a1 += S.f32[q][u];
+                    S.colpart[2][ch][u] = a1;
                 }
-                for (int i = t; i < H * d_in; i += kTcThreads) {
-                    const int u = i / d_in, k = i - u * d_in;
+                if (t < H * d_in) {
+                    const int u = t / d_in, k = t - u * d_in;
                     float acc = 0.0f;
                     for (int q = 0; q < kTcRows; ++q) acc = fmaf(bf(S.f32[q][u]), S.xs[q][k], acc);
-                    part[i] += acc;
+                    part[t] += acc;
+                }
+                __syncthreads();
+                if (t < H) {
+                    float a1 = 0.0f;
+                    for (int ch = 0; ch < kTcChunks; ++ch) a1 += S.colpart[2][ch][t];
+                    part[off_b1(d_in) + t] += a1;
                 }
                 __syncthreads();
             }
