@@ -328,6 +328,19 @@ __device__ __forceinline__ int gap_cells(unsigned long long y57, const GapScale&
     return k >= static_cast<unsigned long long>(n_cells) ? n_cells : static_cast<int>(k);
 }
 
+// Smallest 53-bit u (as an integer) for which the first gap of a set of
+// probability p passes n cells: u >= 1 - (1 - p)^n, i.e. -log(1 - u) >= n mu.
+// At least 1 (u = 0 gives the gap 0) and at most 2^53 (never, for p >= 1).
+// At the boundary this and the gap's own floor can disagree only where
+// E / mu is within a few ulps of n, which the oracle reports as a near tie.
+__device__ __forceinline__ unsigned long long first_gap_none(double p, int n) {
+    if (p >= 1.0) return 1ull << 53;
+    const double q = -expm1(static_cast<double>(n) * log1p(-p));  // 1 - (1 - p)^n
+    const double t = ceil(q * 0x1p53);
+    if (!(t >= 1.0)) return 1ull;
+    return t >= 0x1p53 ? (1ull << 53) : static_cast<unsigned long long>(t);
+}
+
 __device__ __forceinline__ unsigned long long expo_q57(uint32_t lo, uint32_t hi, const LogTable& tab) {
     const unsigned long long bits = (static_cast<unsigned long long>(hi) << 32) | lo;
     return neg_log_q57((1ULL << 53) - (bits >> 11), tab);
@@ -366,8 +379,8 @@ __device__ void draw_events(uint32_t* __restrict__ ev, int n_cells, const GapSca
 template <int NWARP>
 __device__ void draw_step_events(uint32_t* __restrict__ ev_g, uint32_t* __restrict__ ev_h, int n_cells,
                                  bool grow_on, bool light_on, const GapScale& gsg, const GapScale& gsh,
-                                 uint32_t t, uint32_t rep, uint32_t c3g, uint32_t c3h, const RoundKeys& rk,
-                                 const LogTable& tab, int (*tot)[NWARP]) {
+                                 unsigned long long light_none, uint32_t t, uint32_t rep, uint32_t c3g,
+                                 uint32_t c3h, const RoundKeys& rk, const LogTable& tab, int (*tot)[NWARP]) {
     static_assert(NWARP >= 2, "one-warp CTAs draw with draw_events");
     constexpr int NG = NWARP - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -380,17 +393,32 @@ __device__ void draw_step_events(uint32_t* __restrict__ ev_g, uint32_t* __restri
             const bool g = warp < NG;
             const uint32_t c0 = static_cast<uint32_t>(g ? (r * NG + warp) * 32 + lane : r * 32 + lane);
             const uint4 b = philox(c0, t, rep, g ? c3g : c3h, rk);
-            const GapScale& gs = g ? gsg : gsh;
-            k0 = gap_cells(expo_q57(b.x, b.y, tab), gs, n_cells);
-            k1 = gap_cells(expo_q57(b.z, b.w, tab), gs, n_cells);
-            span = 2 + k0 + k1;
-            incl = span;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int v = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl += v;
+            // The lightning set's first gap passes the lattice (no event this
+            // step) iff u >= 1 - (1 - p)^(L^2): one compare of gap 0's 53 bits
+            // instead of the logs and the scan, most steps.
+            bool none = false;
+            if (!g && r == 0) {
+                const unsigned long long bits = ((static_cast<unsigned long long>(b.y) << 32) | b.x) >> 11;
+                none = __shfl_sync(kFull, bits >= light_none ? 1 : 0, 0) != 0;
             }
-            if (lane == 31) tt[warp] = incl;
+            if (none) {
+                k0 = n_cells;
+                k1 = n_cells;
+                incl = n_cells + 1;  // the set ends; no event bits
+                if (lane == 31) tt[warp] = incl;
+            } else {
+                const GapScale& gs = g ? gsg : gsh;
+                k0 = gap_cells(expo_q57(b.x, b.y, tab), gs, n_cells);
+                k1 = gap_cells(expo_q57(b.z, b.w, tab), gs, n_cells);
+                span = 2 + k0 + k1;
+                incl = span;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                if (lane == 31) tt[warp] = incl;
+            }
         }
         __syncthreads();
         int before = 0, total_g = 0;
@@ -449,6 +477,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
     const bool any_grow = p_grow > 0.0, any_light = p_light > 0.0;
     const GapScale gs_grow = any_grow ? gap_scale(p_grow) : GapScale{0ull, 128};
     const GapScale gs_light = any_light ? gap_scale(p_light) : GapScale{0ull, 128};
+    const unsigned long long light_none = any_light ? first_gap_none(p_light, L * L) : (1ull << 53);
     const uint32_t c3_grow = stream_word(5u, dp), c3_light = stream_word(6u, dp);
 
     ff_load_initial<W>(lattice, init, item, t_dens, rep, dp, rk);
@@ -464,8 +493,8 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
             if (any_grow) draw_events(ev_g, L * L, gs_grow, t, rep, c3_grow, rk, tab);
             if (any_light) draw_events(ev_h, L * L, gs_light, t, rep, c3_light, rk, tab);
         } else {
-            draw_step_events<NWARP>(ev_g, ev_h, L * L, any_grow, any_light, gs_grow, gs_light, t, rep, c3_grow,
-                                    c3_light, rk, tab, tot);
+            draw_step_events<NWARP>(ev_g, ev_h, L * L, any_grow, any_light, gs_grow, gs_light, light_none, t, rep,
+                                    c3_grow, c3_light, rk, tab, tot);
         }
         __syncthreads();
         // counts of the steps before t are complete: flush a finished chunk
