@@ -89,10 +89,11 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
 // fraction.  log1p(r) = r - r^2/2 + r^2 (r/3 - r^2/4) (the r^5 term is below
 // 2^-67): r and r^2 in 64-bit fixed point, the bracket and its product with
 // r^2 in 32-bit pieces (one wide multiply), since their weight is below
-// 2^-40.  The result carries an absolute error below 2^-56 (2^-56.96 in an
-// exhaustive check of slice edges and centres at every exponent) before its
-// one rounding to double, i.e. within about an ulp for -log(1 - u) > 1/16
-// and far below the ulp of any sum it enters.
+// 2^-40; n ln 2 comes rounded from a 64-entry table.  The result carries an
+// absolute error below 2^-56 (2^-57.0 in an exhaustive check of slice edges
+// and centres at every exponent) before its one rounding to double, i.e.
+// within about an ulp for -log(1 - u) > 1/16 and far below the ulp of any
+// sum it enters.
 // ---------------------------------------------------------------------------
 constexpr int kLogSliceBits = 12;
 constexpr int kLogSlices = 1 << kLogSliceBits;
@@ -103,8 +104,9 @@ struct __align__(16) LogSlice {
 };
 
 struct LogTable {
-    const LogSlice* slice;       // kLogSlices entries, device memory
-    unsigned long long ln2_q64;  // round(ln 2 * 2^64)
+    const LogSlice* slice;            // kLogSlices entries, device memory
+    const unsigned long long* nln2;   // [n] = round(n ln 2 * 2^57), n = 0..63, device memory
+    unsigned long long ln2_q64;       // round(ln 2 * 2^64)
 };
 
 // Table for the current device (built and uploaded on first use; call it
@@ -119,21 +121,17 @@ __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, 
     const unsigned long long n = static_cast<unsigned long long>(lz - 10);  // 53 - e
     const int j = static_cast<int>((m >> (63 - kLogSliceBits)) & (kLogSlices - 1));
     const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tab.slice) + j);
-    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62, |r 2^64| < 2^51
+    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62 to 2^-62 (the low
+    // product's two bits would add below 2^-62), |r 2^64| < 2^51
     const unsigned long long hi = __umul64hi(m, e.x);
-    const unsigned long long lo = m * e.x;
-    const long long R = static_cast<long long>(((hi - (1ULL << 62)) << 2) | (lo >> 62));
+    const long long R = static_cast<long long>((hi - (1ULL << 62)) << 2);
     const long long r2 = __mul64hi(R, R);                               // r^2 2^64 < 2^38
     const int a = static_cast<int>(R >> 20);                            // r 2^44
     const int q = __mulhi(a, 1431655766) - static_cast<int>(r2 >> 22);  // (r/3 - r^2/4) 2^44
     const long long tail = (static_cast<long long>(static_cast<int>(r2 >> 7)) * q) >> 37;  // r^2 q 2^64
     const long long l1p = R - (r2 >> 1) + tail;                          // log1p(r) 2^64
     const long long s63 = static_cast<long long>(e.y >> 1) + (l1p >> 1);  // ln M 2^63
-    // n ln2 2^57, rounded (n <= 53, so the product stays below 2^70)
-    const unsigned long long p_lo = n * tab.ln2_q64;
-    const unsigned long long p_hi = __umul64hi(n, tab.ln2_q64);
-    const unsigned long long r_lo = p_lo + 64u;
-    const unsigned long long nln2 = ((p_hi + (r_lo < p_lo ? 1u : 0u)) << 57) | (r_lo >> 7);
+    const unsigned long long nln2 = __ldg(tab.nln2 + n);  // n ln2 2^57, rounded (n <= 53)
     // near y = 0 (K close to 2^53) the roundings may undershoot: clamp
     const long long y = static_cast<long long>(nln2) - ((s63 + 32) >> 6);
     return y > 0 ? static_cast<unsigned long long>(y) : 0ULL;

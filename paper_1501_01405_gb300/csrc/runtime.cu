@@ -98,12 +98,23 @@ void build_log_slices(std::vector<LogSlice>& t) {
 mrip_status log_table(LogTable* out) {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     DeviceScratch& d = dev_scratch();
+    const unsigned long long ln2_q64 = static_cast<unsigned long long>(ldexpl(logl(2.0L), 64) + 0.5L);
     if (!d.log_slices) {
         std::vector<LogSlice> t;
         build_log_slices(t);
+        // n ln2 2^57 rounded, from the 128-bit product n * round(ln2 2^64)
+        std::vector<unsigned long long> nln2(64);
+        for (unsigned n = 0; n < 64; ++n) {
+            const unsigned __int128 prod = static_cast<unsigned __int128>(n) * ln2_q64 + 64u;
+            nln2[n] = static_cast<unsigned long long>(prod >> 7);
+        }
+        const size_t slice_bytes = t.size() * sizeof(LogSlice);
         LogSlice* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, t.size() * sizeof(LogSlice));
-        if (e == cudaSuccess) e = cudaMemcpy(p, t.data(), t.size() * sizeof(LogSlice), cudaMemcpyHostToDevice);
+        cudaError_t e = cudaMalloc(&p, slice_bytes + nln2.size() * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemcpy(p, t.data(), slice_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(reinterpret_cast<char*>(p) + slice_bytes, nln2.data(),
+                           nln2.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             if (p) cudaFree(p);
             return cuda_status(e, "log table upload");
@@ -111,7 +122,8 @@ mrip_status log_table(LogTable* out) {
         d.log_slices = p;
     }
     out->slice = d.log_slices;
-    out->ln2_q64 = static_cast<unsigned long long>(ldexpl(logl(2.0L), 64) + 0.5L);
+    out->nln2 = reinterpret_cast<const unsigned long long*>(d.log_slices + kLogSlices);
+    out->ln2_q64 = ln2_q64;
     return MRIP_OK;
 }
 
