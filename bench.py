@@ -534,6 +534,32 @@ def pi_sweep(eng, torch, n_draws=10**7, runs=7):
     return out
 
 
+def mm1_sweep(eng, torch, runs=5):
+    """M/M/1 (lambda 0.9, mu 1) mappings against the replication count and
+    length: time per launch (median of `runs`, CUDA events)."""
+    d = torch.tensor([[0.9, 1.0]], dtype=torch.float64, device="cuda")
+    out = {"cases": [], "ms": {"THREAD": [], "WARP_1LANE": [], "WARP_COOP": [], "CTA": []}}
+    for n_reps, n_clients in ((1, 10**5), (32, 1000), (32, 10**4), (1024, 1000), (1 << 16, 1000)):
+        w = torch.empty(n_reps, dtype=torch.float64, device="cuda")
+        out["cases"].append([n_reps, n_clients])
+        for mp in out["ms"]:
+            if mp == "WARP_1LANE" and n_reps > 1024:
+                out["ms"][mp].append(None)
+                continue
+            times = []
+            for r in range(runs + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                eng.mrip_mm1_simulate(d, n_reps, n_clients, 42, getattr(eng, "MRIP_MAP_" + mp), w)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            out["ms"][mp].append(float(np.median(times)))
+    return out
+
+
 def tandem_sweep(eng, torch, n_clients=10**5, runs=5):
     """Few replications of a long horizon: time per launch (median of `runs`,
     CUDA events) of each tandem mapping for 1 .. 16,384 replications of
@@ -878,7 +904,7 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="area_walk: time every mapping for 1 .. 2^16 replications; "
                          "pi: time 1 .. 256 replications; tandem: mappings for 1 .. 16,384 "
-                         "replications of 10^5 clients")
+                         "replications of 10^5 clients; mm1_32: M/M/1 mappings")
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-dp", type=int, default=0,
@@ -915,9 +941,10 @@ def main():
             dist.barrier()
 
     if args.sweep:
-        sweeps = {"area_walk": area_walk_sweep, "pi": pi_sweep, "tandem": tandem_sweep}
+        sweeps = {"area_walk": area_walk_sweep, "pi": pi_sweep, "tandem": tandem_sweep,
+                  "mm1_32": mm1_sweep}
         if args.workload not in sweeps:
-            raise SystemExit("--sweep applies to --workload area_walk, pi or tandem")
+            raise SystemExit("--sweep applies to --workload area_walk, pi, tandem or mm1_32")
         if rank == 0:
             print(json.dumps({"metric": METRIC, "sweep": sweeps[args.workload](eng, torch),
                               "config": wl.config()}), flush=True)
