@@ -73,6 +73,14 @@ __device__ __forceinline__ uint4 philox_step(unsigned long long prod, uint32_t c
     return make_uint4(x0, x1, x2, x3);
 }
 
+// bits |= bit if w < t, as a compare and a predicated OR (integer ALU, not the
+// multiply pipe that Philox saturates).
+__device__ __forceinline__ void or_if_below(uint32_t& bits, uint32_t w, uint32_t t, uint32_t bit) {
+    asm("{\n .reg .pred p;\n setp.lt.u32 p, %1, %2;\n @p or.b32 %0, %0, %3;\n}\n"
+        : "+r"(bits)
+        : "r"(w), "r"(t), "r"(bit));
+}
+
 // Threads per CTA for a lattice of W words per row.
 template <int W>
 constexpr int ff_threads() {
@@ -208,10 +216,10 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const uint4 b = philox_step(base + 0xD2511F53ull * q, c3, sk, rk);
-                g |= (b.x < t_grow) ? (1u << (4 * q)) : 0u;
-                g |= (b.y < t_grow) ? (1u << (4 * q + 1)) : 0u;
-                g |= (b.z < t_grow) ? (1u << (4 * q + 2)) : 0u;
-                g |= (b.w < t_grow) ? (1u << (4 * q + 3)) : 0u;
+                or_if_below(g, b.x, t_grow, 1u << (4 * q));
+                or_if_below(g, b.y, t_grow, 1u << (4 * q + 1));
+                or_if_below(g, b.z, t_grow, 1u << (4 * q + 2));
+                or_if_below(g, b.w, t_grow, 1u << (4 * q + 3));
                 const uint32_t lowest = min(min(b.x, b.y), min(b.z, b.w));
                 if (__builtin_expect(lowest < t_light, 0)) {
                     l |= (b.x < t_light) ? (1u << (4 * q)) : 0u;
