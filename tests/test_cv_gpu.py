@@ -157,6 +157,20 @@ def test_run_cv_tandem_matches_oracle_pipeline(env):
     m.close()
 
 
+def test_run_cv_large_minibatch_matches_oracle_pipeline(env):
+    """Minibatches of 2,048: each of the training cluster's CTAs takes two tiles
+    of 128 samples per step (its gradient accumulates over both)."""
+    eng, torch = env
+    dps = mrip_inputs.tandem_design_points(16, seed=21)
+    kw = dict(train_frac=0.25, epochs=3, batch=2048, lr=3e-3, m_ctrl=60)
+    m = eng.Model(eng.MRIP_TANDEM3, n_clients=150, window=40)
+    plain, cv, loss = m.run_cv(dps, 600, 9, **kw)
+    ref_plain, ref_cv, ref_loss = ocv.run_cv("tandem3", dps, 600, 9, n_clients=150, window=40,
+                                             threads=oracle.host_threads(), **kw)
+    _compare_pipeline(plain, cv, loss, ref_plain, ref_cv, ref_loss)
+    m.close()
+
+
 def test_run_cv_forest_fire_matches_oracle_pipeline(env):
     eng, torch = env
     dps = mrip_inputs.ff_cv_design_points(4)
