@@ -564,7 +564,8 @@ def tandem_sweep(eng, torch, n_clients=10**5, runs=5):
     """Few replications of a long horizon: time per launch (median of `runs`,
     CUDA events) of each tandem mapping for 1 .. 16,384 replications of
     10^5 clients at one design point (lambda 0.9, mu 1.0, 1.1, 1.2)."""
-    out = {"n_clients": n_clients, "reps": [], "ms": {"THREAD": [], "WARP_1LANE": [], "WARP_COOP": []}}
+    out = {"n_clients": n_clients, "reps": [],
+           "ms": {"THREAD": [], "WARP_1LANE": [], "WARP_COOP": [], "CTA": []}}
     dps = torch.tensor([[0.9, 1.0, 1.1, 1.2]], dtype=torch.float64, device="cuda")
     for k in range(0, 15, 2):
         n = 1 << k

@@ -241,10 +241,11 @@ mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
  * d_feat (may be NULL): device 8 planes of n_dp * n_reps: lambda, mu1..3 and
  * the means over the first min(window, n_clients) clients of A, S1, S2, S3.
  * If n_clients == window only the early window is simulated (control runs).
- * mapping: THREAD, WARP_1LANE or WARP_COOP (one replication per warp: lanes
+ * mapping: THREAD, WARP_1LANE, WARP_COOP (one replication per warp: lanes
  * take 32 contiguous client segments, a warp scan of their max-plus maps gives
- * each segment's entry state; for few replications of many clients).
- * AUTO = THREAD. */
+ * each segment's entry state) or CTA (the same over up to 1,024 threads, ~4
+ * clients each, with a block scan); the last two are for few replications of
+ * many clients.  AUTO = THREAD. */
 mrip_status mrip_tandem3_simulate(const double *d_dps, int32_t n_dp, int64_t rep0,
                                   int64_t n_reps, int64_t n_clients, int64_t window,
                                   uint64_t seed, uint32_t tag, int mapping, double *d_y,

@@ -293,7 +293,7 @@ bool mapping_allowed(int kind, int mapping) {
                    mapping == MRIP_MAP_WARP_1LANE || mapping == MRIP_MAP_WARP_COOP || mapping == MRIP_MAP_CTA;
         case MRIP_TANDEM3:
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE ||
-                   mapping == MRIP_MAP_WARP_COOP;
+                   mapping == MRIP_MAP_WARP_COOP || mapping == MRIP_MAP_CTA;
         case MRIP_FOREST_FIRE: return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_CTA;
         case MRIP_WALK_L1_EXIT:
             return mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD || mapping == MRIP_MAP_WARP_1LANE ||
@@ -321,6 +321,7 @@ std::vector<Plan> candidates(int kind) {
             break;
         case MRIP_TANDEM3:
             add(MRIP_MAP_THREAD, 0, 0, 0);
+            add(MRIP_MAP_CTA, 0, 0, 0);
             add(MRIP_MAP_WARP_COOP, 0, 0, 0);
             add(MRIP_MAP_WARP_1LANE, 0, 0, 0);
             break;

@@ -506,6 +506,89 @@ __device__ __forceinline__ FTMap ftmap_shfl_up(const FTMap& m, int off) {
     return r;
 }
 
+// FP64 warp scan of one replication (the fallback of the fixed-point paths):
+// lane l takes the l-th of 32 contiguous client segments.
+__device__ void tandem_coop_fp64(long long item, uint32_t dp, uint32_t rep, double lam, double mu1, double mu2,
+                                 double mu3, long long n_clients, long long window, uint32_t c3,
+                                 const RoundKeys& rk, const LogTable& tab, const TandemOut& out) {
+    (void)dp;
+    const int lane = threadIdx.x & 31;
+    const double i_lam = 0x1p-57 / lam, i_mu1 = 0x1p-57 / mu1, i_mu2 = 0x1p-57 / mu2, i_mu3 = 0x1p-57 / mu3;
+    const long long w_len = (n_clients < window) ? n_clients : window;
+    const long long seg = (n_clients + 31) / 32;
+    const long long lo = min(lane * seg, n_clients);
+    const long long hi = min(lo + seg, n_clients);
+    // pass 1: this segment's map
+    TMap f = tmap_identity();
+    for (long long n = lo; n < hi; ++n) {
+        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
+        f = tmap_push(f, k.a, k.s1, k.s2, k.s3);
+    }
+    // inclusive scan over lanes, then the previous lane's prefix is the entry map
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const TMap prev = tmap_shfl_up(f, off);
+        if (lane >= off) f = tmap_compose(prev, f);
+    }
+    const TMap excl = tmap_shfl_up(f, 1);
+    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
+    if (lane > 0) {
+        v1 = excl.c1;
+        v2 = excl.c2;
+        v3 = excl.c3;
+    }
+
+    // pass 2: replay the segment with the plain recurrence
+    double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
+    for (long long n = lo; n < hi; ++n) {
+        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
+        double q = v1 - k.a;
+        v1 = ((q > 0.0) ? q : 0.0) + k.s1;
+        q = v2 - k.a;
+        v2 = ((q > v1) ? q : v1) + k.s2;
+        q = v3 - k.a;
+        v3 = ((q > v2) ? q : v2) + k.s3;
+        sum_y += v3;
+        if (n < w_len) {
+            sum_a += k.a;
+            sum_1 += k.s1;
+            sum_2 += k.s2;
+            sum_3 += k.s3;
+        }
+    }
+    // fixed-order (lane-ordered tree) reduction
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double oy = __shfl_down_sync(kFull, sum_y, off);
+        const double oa = __shfl_down_sync(kFull, sum_a, off);
+        const double o1 = __shfl_down_sync(kFull, sum_1, off);
+        const double o2 = __shfl_down_sync(kFull, sum_2, off);
+        const double o3 = __shfl_down_sync(kFull, sum_3, off);
+        if ((lane & (2 * off - 1)) == 0) {
+            sum_y += oy;
+            sum_a += oa;
+            sum_1 += o1;
+            sum_2 += o2;
+            sum_3 += o3;
+        }
+    }
+    if (lane != 0) return;
+    out.y[item] = sum_y / static_cast<double>(n_clients);
+    if (out.feat) {
+        const double wl = static_cast<double>(w_len);
+        double* fo = out.feat + item;
+        const long long p = out.plane;
+        fo[0] = lam;
+        fo[p] = mu1;
+        fo[2 * p] = mu2;
+        fo[3 * p] = mu3;
+        fo[4 * p] = sum_a / wl;
+        fo[5 * p] = sum_1 / wl;
+        fo[6 * p] = sum_2 / wl;
+        fo[7 * p] = sum_3 / wl;
+    }
+}
+
 __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
     const double* __restrict__ dps, long long n_items, long long n_reps, long long rep0,
     long long n_clients, long long window, uint32_t tag, const __grid_constant__ RoundKeys rk,
@@ -609,75 +692,8 @@ __global__ void __launch_bounds__(128) tandem3_warp_coop_kernel(
         }
     }
 
-    // FP64: pass 1, this segment's map
-    TMap f = tmap_identity();
-    for (long long n = lo; n < hi; ++n) {
-        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
-        f = tmap_push(f, k.a, k.s1, k.s2, k.s3);
-    }
-    // inclusive scan over lanes, then the previous lane's prefix is the entry map
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const TMap prev = tmap_shfl_up(f, off);
-        if (lane >= off) f = tmap_compose(prev, f);
-    }
-    const TMap excl = tmap_shfl_up(f, 1);
-    double v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
-    if (lane > 0) {
-        v1 = excl.c1;
-        v2 = excl.c2;
-        v3 = excl.c3;
-    }
-
-    // pass 2: replay the segment with the plain recurrence
-    double sum_y = 0.0, sum_a = 0.0, sum_1 = 0.0, sum_2 = 0.0, sum_3 = 0.0;
-    for (long long n = lo; n < hi; ++n) {
-        const TandemClient k = tandem_client(static_cast<uint32_t>(n), rep, c3, rk, tab, i_lam, i_mu1, i_mu2, i_mu3);
-        double q = v1 - k.a;
-        v1 = ((q > 0.0) ? q : 0.0) + k.s1;
-        q = v2 - k.a;
-        v2 = ((q > v1) ? q : v1) + k.s2;
-        q = v3 - k.a;
-        v3 = ((q > v2) ? q : v2) + k.s3;
-        sum_y += v3;
-        if (n < w_len) {
-            sum_a += k.a;
-            sum_1 += k.s1;
-            sum_2 += k.s2;
-            sum_3 += k.s3;
-        }
-    }
-    // fixed-order (lane-ordered tree) reduction
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const double oy = __shfl_down_sync(kFull, sum_y, off);
-        const double oa = __shfl_down_sync(kFull, sum_a, off);
-        const double o1 = __shfl_down_sync(kFull, sum_1, off);
-        const double o2 = __shfl_down_sync(kFull, sum_2, off);
-        const double o3 = __shfl_down_sync(kFull, sum_3, off);
-        if ((lane & (2 * off - 1)) == 0) {
-            sum_y += oy;
-            sum_a += oa;
-            sum_1 += o1;
-            sum_2 += o2;
-            sum_3 += o3;
-        }
-    }
-    if (lane != 0) return;
-    out.y[item] = sum_y / static_cast<double>(n_clients);
-    if (out.feat) {
-        const double wl = static_cast<double>(w_len);
-        double* fo = out.feat + item;
-        const long long p = out.plane;
-        fo[0] = lam;
-        fo[p] = mu1;
-        fo[2 * p] = mu2;
-        fo[3 * p] = mu3;
-        fo[4 * p] = sum_a / wl;
-        fo[5 * p] = sum_1 / wl;
-        fo[6 * p] = sum_2 / wl;
-        fo[7 * p] = sum_3 / wl;
-    }
+    // FP64
+    tandem_coop_fp64(item, dp, rep, lam, mu1, mu2, mu3, n_clients, window, c3, rk, tab, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -869,6 +885,144 @@ __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tandem, one replication per CTA (few replications of a long horizon): thread
+// i takes the contiguous clients [i k, (i+1) k); its fixed-point max-plus map
+// (FTMap) is composed in pass 1, a block scan (warp shuffles, then the warp
+// totals in order) gives every thread the map of all clients before it, and
+// pass 2 replays its clients from that entry state.  Sojourn sums are exact
+// 128-bit integers; the early-window sums FP64 in a fixed order.  Rates
+// outside the fixed-point range or a sojourn past 2^12 hand the replication
+// to the FP64 warp scan (warp 0).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) tandem3_cta_kernel(const double* __restrict__ dps, long long n_reps,
+                                                           long long rep0, long long n_clients, long long window,
+                                                           uint32_t tag, const __grid_constant__ RoundKeys rk,
+                                                           LogTable tab, TandemOut out) {
+    __shared__ FTMap wmap[32];
+    __shared__ U128 wy[32];
+    __shared__ double wsum[4][32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
+    const long long item = blockIdx.x;
+    const uint32_t dp = static_cast<uint32_t>(item / n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
+    const double lam = dps[4 * dp], mu1 = dps[4 * dp + 1], mu2 = dps[4 * dp + 2], mu3 = dps[4 * dp + 3];
+    const uint32_t c3 = stream_word(tag, dp);
+    const long long w_len = (n_clients < window) ? n_clients : window;
+    const long long k = (n_clients + blockDim.x - 1) / blockDim.x;
+    const long long lo = min(static_cast<long long>(t) * k, n_clients);
+    const long long hi = min(lo + k, n_clients);
+
+    if (fix_rate_ok(lam) && fix_rate_ok(mu1) && fix_rate_ok(mu2) && fix_rate_ok(mu3)) {
+        const unsigned long long cl = fix_scale(lam), c1 = fix_scale(mu1), c2 = fix_scale(mu2),
+                                 c3f = fix_scale(mu3);
+        FTMap f = ftmap_identity();
+        for (long long n = lo; n < hi; ++n) {
+            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            f = ftmap_push(f, to_fix(neg_log_q57(word_k(b0.x, b0.y), tab), cl),
+                           to_fix(neg_log_q57(word_k(b0.z, b0.w), tab), c1),
+                           to_fix(neg_log_q57(word_k(b1.x, b1.y), tab), c2),
+                           to_fix(neg_log_q57(word_k(b1.z, b1.w), tab), c3f));
+        }
+        // block exclusive scan of the maps
+        FTMap incl = f;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const FTMap prev = ftmap_shfl_up(incl, off);
+            if (lane >= off) incl = ftmap_compose(prev, incl);
+        }
+        if (lane == 31) wmap[warp] = incl;
+        __syncthreads();
+        FTMap pre = ftmap_identity();
+        for (int w = 0; w < warp; ++w) pre = ftmap_compose(pre, wmap[w]);
+        FTMap excl = ftmap_shfl_up(incl, 1);
+        if (lane == 0) excl = ftmap_identity();
+        pre = ftmap_compose(pre, excl);
+        long long v1 = pre.c1, v2 = pre.c2, v3 = pre.c3;  // -2^61 for the first thread: empty
+        bool bad = v3 >= kFixGuard;
+        U128 sy;
+        double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+        const double i_lam = 0x1p-57 / lam, i_mu1 = 0x1p-57 / mu1, i_mu2 = 0x1p-57 / mu2,
+                     i_mu3 = 0x1p-57 / mu3;
+        for (long long n = lo; n < hi && !bad; ++n) {
+            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            const unsigned long long ya = neg_log_q57(word_k(b0.x, b0.y), tab);
+            const unsigned long long y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
+            const unsigned long long y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
+            const unsigned long long y3 = neg_log_q57(word_k(b1.z, b1.w), tab);
+            const long long a = to_fix(ya, cl);
+            long long q = v1 - a;
+            v1 = ((q > 0) ? q : 0) + to_fix(y1, c1);
+            q = v2 - a;
+            v2 = ((q > v1) ? q : v1) + to_fix(y2, c2);
+            q = v3 - a;
+            v3 = ((q > v2) ? q : v2) + to_fix(y3, c3f);
+            sy.add(v3);
+            if (n < w_len) {
+                wa += __ull2double_rn(ya) * i_lam;
+                w1 += __ull2double_rn(y1) * i_mu1;
+                w2 += __ull2double_rn(y2) * i_mu2;
+                w3 += __ull2double_rn(y3) * i_mu3;
+            }
+            bad = v3 >= kFixGuard;
+        }
+        if (!__syncthreads_or(bad)) {
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {  // lane-ordered tree (integers: exact)
+                const U128 oy = shfl_down_u128(sy, off);
+                const double oa = __shfl_down_sync(kFull, wa, off);
+                const double o1 = __shfl_down_sync(kFull, w1, off);
+                const double o2 = __shfl_down_sync(kFull, w2, off);
+                const double o3 = __shfl_down_sync(kFull, w3, off);
+                if ((lane & (2 * off - 1)) == 0) {
+                    add_u128(sy, oy);
+                    wa += oa;
+                    w1 += o1;
+                    w2 += o2;
+                    w3 += o3;
+                }
+            }
+            if (lane == 0) {
+                wy[warp] = sy;
+                wsum[0][warp] = wa;
+                wsum[1][warp] = w1;
+                wsum[2][warp] = w2;
+                wsum[3][warp] = w3;
+            }
+            __syncthreads();
+            if (t == 0) {
+                U128 ty;
+                double sa = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int w = 0; w < nwarp; ++w) {
+                    add_u128(ty, wy[w]);
+                    sa += wsum[0][w];
+                    s1 += wsum[1][w];
+                    s2 += wsum[2][w];
+                    s3 += wsum[3][w];
+                }
+                out.y[item] = ty.to_double() / static_cast<double>(n_clients);
+                if (out.feat) {
+                    const double wl = static_cast<double>(w_len);
+                    double* fo = out.feat + item;
+                    const long long p = out.plane;
+                    fo[0] = lam;
+                    fo[p] = mu1;
+                    fo[2 * p] = mu2;
+                    fo[3 * p] = mu3;
+                    fo[4 * p] = sa / wl;
+                    fo[5 * p] = s1 / wl;
+                    fo[6 * p] = s2 / wl;
+                    fo[7 * p] = s3 / wl;
+                }
+            }
+            return;
+        }
+    }
+    if (warp == 0) tandem_coop_fp64(item, dp, rep, lam, mu1, mu2, mu3, n_clients, window, c3, rk, tab, out);
+}
+
 }  // namespace
 }  // namespace mrip
 
@@ -963,8 +1117,15 @@ extern "C" mrip_status mrip_tandem3_simulate(const double* d_dps, int32_t n_dp, 
     } else if (mapping == MRIP_MAP_WARP_COOP) {
         tandem3_warp_coop_kernel<<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
             d_dps, n_items, n_reps, rep0, n_clients, window, tag, rk, tab, out);
+    } else if (mapping == MRIP_MAP_CTA) {
+        if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_tandem3_simulate: too many replications for CTA");
+        // about 4 clients per thread, 32 .. 1024 threads
+        long long threads = ((n_clients + 3) / 4 + 31) / 32 * 32;
+        threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+        tandem3_cta_kernel<<<static_cast<unsigned>(n_items), static_cast<unsigned>(threads), 0, st>>>(
+            d_dps, n_reps, rep0, n_clients, window, tag, rk, tab, out);
     } else {
-        return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");
+        return fail(MRIP_EINVAL, "mrip_tandem3_simulate: mapping must be THREAD, WARP_1LANE, WARP_COOP or CTA");
     }
     return launch_status("mrip_tandem3_simulate");
 }

@@ -142,7 +142,7 @@ def test_tandem_thread_and_wlp(eng, torch_mod):
     n_reps, n_clients, window = 7, 2000, 100
     ref_y, ref_f = oracle.tandem3(dps, *oracle.all_items(5, n_reps), n_clients, 42,
                                   window=window, threads=threads())
-    for mapping in (eng.MRIP_MAP_THREAD, eng.MRIP_MAP_WARP_1LANE, eng.MRIP_MAP_WARP_COOP):
+    for mapping in (eng.MRIP_MAP_THREAD, eng.MRIP_MAP_WARP_1LANE, eng.MRIP_MAP_WARP_COOP, eng.MRIP_MAP_CTA):
         y = t.empty(5 * n_reps, dtype=t.float64, device="cuda")
         f = t.empty(8 * 5 * n_reps, dtype=t.float64, device="cuda")
         eng.mrip_tandem3_simulate(dev(t, dps), 0, n_reps, n_clients, window, 42, 0, mapping, y, f)
@@ -150,7 +150,7 @@ def test_tandem_thread_and_wlp(eng, torch_mod):
         np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, ref_f, rtol=REL)
 
 
-@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP"])
+@pytest.mark.parametrize("mapping", ["THREAD", "WARP_1LANE", "WARP_COOP", "CTA"])
 def test_tandem_fixed_point_fallbacks(eng, torch_mod, mapping):
     """Times run in 48-bit fixed point; a slow rate (below 2^-6) sends a design
     point to FP64 and an unstable queue whose sojourn time passes 2^12
@@ -190,8 +190,10 @@ def test_tandem_offset_tag_and_short_runs(eng, torch_mod):
     np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
 
 
-@pytest.mark.parametrize("n_clients,window", [(1, 1), (31, 5), (33, 100), (1000, 64), (100003, 4096)])
-def test_tandem_warp_coop_ragged(eng, torch_mod, n_clients, window):
+@pytest.mark.parametrize("mapping", ["WARP_COOP", "CTA"])
+@pytest.mark.parametrize("n_clients,window", [(1, 1), (31, 5), (33, 100), (1000, 64), (4099, 100),
+                                              (100003, 4096)])
+def test_tandem_warp_coop_ragged(eng, torch_mod, n_clients, window, mapping):
     """Warp scan over 32 client segments: fewer clients than lanes, a
     ragged last segment, window shorter and longer than a segment, a long
     horizon; offset replications and a non-zero stream tag."""
@@ -204,7 +206,7 @@ def test_tandem_warp_coop_ragged(eng, torch_mod, n_clients, window):
     y = t.empty(3 * n_reps, dtype=t.float64, device="cuda")
     f = t.empty(8 * 3 * n_reps, dtype=t.float64, device="cuda")
     eng.mrip_tandem3_simulate(dev(t, dps), rep0, n_reps, n_clients, window, 42, 2,
-                              eng.MRIP_MAP_WARP_COOP, y, f)
+                              getattr(eng, "MRIP_MAP_" + mapping), y, f)
     np.testing.assert_allclose(y.cpu().numpy(), ry, rtol=REL)
     np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
 
