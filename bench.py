@@ -64,7 +64,7 @@ MULS_PER_FIXED_VARIATE = 34
 
 # DRAM bytes (read + write) per launch of a dominant kernel, from the ncu
 # capture summarised in profiles/ (None once the kernel changes).
-PROFILED_TRAFFIC = {"forest_fire_kernel<4>": 39936}
+PROFILED_TRAFFIC = {"forest_fire_kernel<4>": 36864}
 
 
 def imul_peak_gops():
