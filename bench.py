@@ -19,7 +19,9 @@ value   = replications / s over the K timed steps, inputs resident in HBM,
 e2e     = the same through the public model-handle API (mrip_run with host
           design points + mrip_stats reading the intervals back), wall time.
 roofline= the dominant kernel's algorithmic work per launch / its mean event
-          time, against the peak derived in the design doc.
+          time, against the nominal integer-multiply rate (SMs x multiplies
+          per clock x maximum SM clock): every model is bound by Philox's
+          32x32->64 products, not by HBM or the tensor cores.
 cpu_baseline = the oracle (plain C) on a bounded sample of the same workload
           on all host cores (rank 0, N = 1 only).
 

@@ -131,7 +131,7 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const long long window = tandem ? m->tandem.window : m->ff.window;
     if (!tandem && window < 4) return fail(MRIP_EINVAL, "mrip_run_cv: forest-fire window must be >= 4 steps");
 
-    // 1. plain run (the judge) and its intervals
+    // 1. plain run (the reference estimate and fallback) and its intervals
     mrip_status s = mrip_run(m, dps, n_dp, n_reps, seed);
     if (s != MRIP_OK) return s;
     s = mrip_stats(m, p->conf, plain_out);

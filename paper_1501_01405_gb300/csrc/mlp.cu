@@ -2,7 +2,7 @@
 // network (d_in = 8 for the tandem queue, 6 for the forest fire) trained on
 // replications the engine generates, used as a control variate.  The paper
 // has no learned component; its estimator (the replication mean, Section 1)
-// stays the fallback and the judge.
+// stays the fallback and the yardstick the control variate is checked against.
 //
 // Arithmetic: parameters are FP32 masters; every matmul takes BF16 operands
 // (round to nearest even from FP32) and accumulates in FP32:
