@@ -87,9 +87,11 @@ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
 // c_j the centre of the j-th of 4096 slices of [1, 2) (j = the 12 bits after
 // the leading one), 1/c_j stored as a 63-bit fraction, ln c_j as a 64-bit
 // fraction.  log1p(r) = r - r^2/2 + r^2 (r/3 - r^2/4) (the r^5 term is below
-// 2^-67): r and r^2 in 64-bit fixed point, the bracket and its product with
-// r^2 in 32-bit pieces (one wide multiply), since their weight is below
-// 2^-40; n ln 2 comes rounded from a 64-entry table.  The result carries an
+// 2^-67): r in 64-bit fixed point; r^2 from r's top 32 bits and one cross
+// product (two 32x32 multiplies instead of a signed 64x64 high product, to
+// 2^-64); the bracket and its product with r^2 in 32-bit pieces (one wide
+// multiply), since their weight is below 2^-40; ln c_j + log1p(r) is summed
+// and rounded once, unsigned; n ln 2 comes rounded from a 64-entry table.  The result carries an
 // absolute error below 2^-56 (2^-57.0 in an exhaustive check of slice edges
 // and centres at every exponent) before its one rounding to double, i.e.
 // within about an ulp for -log(1 - u) > 1/16 and far below the ulp of any
@@ -125,15 +127,20 @@ __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, 
     // product's two bits would add below 2^-62), |r 2^64| < 2^51
     const unsigned long long hi = __umul64hi(m, e.x);
     const long long R = static_cast<long long>((hi - (1ULL << 62)) << 2);
-    const long long r2 = __mul64hi(R, R);                               // r^2 2^64 < 2^38
-    const int a = static_cast<int>(R >> 20);                            // r 2^44
+    const int a = static_cast<int>(R >> 20);       // r 2^44, |a| < 2^31
+    const int rho = static_cast<int>(R & 0xFFFFF);  // R = a 2^20 + rho
+    // r^2 2^64 = (a^2 + a rho 2^-19) 2^-24 + rho^2 2^-64 (< 2^-24, dropped); < 2^38
+    const long long r2 =
+        (static_cast<long long>(a) * a + ((static_cast<long long>(a) * rho) >> 19)) >> 24;
     const int q = __mulhi(a, 1431655766) - static_cast<int>(r2 >> 22);  // (r/3 - r^2/4) 2^44
     const long long tail = (static_cast<long long>(static_cast<int>(r2 >> 7)) * q) >> 37;  // r^2 q 2^64
     const long long l1p = R - (r2 >> 1) + tail;                          // log1p(r) 2^64
-    const long long s63 = static_cast<long long>(e.y >> 1) + (l1p >> 1);  // ln M 2^63
+    // ln M 2^64 + 2^6: below 2^64 (ln M < ln 2) and, the roundings being a
+    // few units, never below zero, so the unsigned sum does not wrap
+    const unsigned long long s64 = e.y + static_cast<unsigned long long>(l1p) + 64u;
     const unsigned long long nln2 = __ldg(tab.nln2 + n);  // n ln2 2^57, rounded (n <= 53)
     // near y = 0 (K close to 2^53) the roundings may undershoot: clamp
-    const long long y = static_cast<long long>(nln2) - ((s63 + 32) >> 6);
+    const long long y = static_cast<long long>(nln2) - static_cast<long long>(s64 >> 7);
     return y > 0 ? static_cast<unsigned long long>(y) : 0ULL;
 }
 

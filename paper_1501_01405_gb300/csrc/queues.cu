@@ -299,13 +299,18 @@ __global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __
         U128 sy;
         double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
         bool overflow = false;
-        for (long long n = 0; n < n_clients; ++n) {
+        // client n's four log values; then one step of the recurrence
+        auto logs = [&](long long n, unsigned long long& ya, unsigned long long& y1, unsigned long long& y2,
+                        unsigned long long& y3) {
             const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
             const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
-            const unsigned long long ya = neg_log_q57(word_k(b0.x, b0.y), tab);
-            const unsigned long long y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
-            const unsigned long long y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
-            const unsigned long long y3 = neg_log_q57(word_k(b1.z, b1.w), tab);
+            ya = neg_log_q57(word_k(b0.x, b0.y), tab);
+            y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
+            y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
+            y3 = neg_log_q57(word_k(b1.z, b1.w), tab);
+        };
+        auto step = [&](unsigned long long ya, unsigned long long y1, unsigned long long y2,
+                        unsigned long long y3) {
             const long long a = to_fix(ya, fl);
             long long q = v1 - a;
             v1 = ((q > 0) ? q : 0) + to_fix(y1, f1);
@@ -314,16 +319,27 @@ __global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __
             q = v3 - a;
             v3 = ((q > v2) ? q : v2) + to_fix(y3, f3);
             sy.add(v3);
-            if (n < w_len) {  // the same variates as doubles (expo_fast)
-                wa += __ull2double_rn(ya) * i_lam;
-                w1 += __ull2double_rn(y1) * i_mu1;
-                w2 += __ull2double_rn(y2) * i_mu2;
-                w3 += __ull2double_rn(y3) * i_mu3;
-            }
-            if (v3 >= kFixGuard) {
+            return v3 < kFixGuard;
+        };
+        // the early window also sums the same variates as doubles (expo_fast);
+        // the loop after it carries none of that state
+        long long n = 0;
+        for (; n < w_len; ++n) {
+            unsigned long long ya, y1, y2, y3;
+            logs(n, ya, y1, y2, y3);
+            wa += __ull2double_rn(ya) * i_lam;
+            w1 += __ull2double_rn(y1) * i_mu1;
+            w2 += __ull2double_rn(y2) * i_mu2;
+            w3 += __ull2double_rn(y3) * i_mu3;
+            if (!step(ya, y1, y2, y3)) {
                 overflow = true;
                 break;
             }
+        }
+        for (; !overflow && n < n_clients; ++n) {
+            unsigned long long ya, y1, y2, y3;
+            logs(n, ya, y1, y2, y3);
+            if (!step(ya, y1, y2, y3)) overflow = true;
         }
         if (!overflow) {
             fixed_done = true;
