@@ -115,6 +115,15 @@ struct LogTable {
 // outside stream capture before the first launch that needs it).
 mrip_status log_table(LogTable* out);
 
+// High 64 bits of a 64 x 64-bit product, short by 0, 1 or 2 units: of the
+// four 32 x 32 partial products the lowest is dropped and the two middle ones
+// enter by their high halves only (one wide multiply and two high products).
+__device__ __forceinline__ unsigned long long umul64hi_trunc(unsigned long long a, unsigned long long b) {
+    const uint32_t ah = static_cast<uint32_t>(a >> 32), al = static_cast<uint32_t>(a);
+    const uint32_t bh = static_cast<uint32_t>(b >> 32), bl = static_cast<uint32_t>(b);
+    return static_cast<unsigned long long>(ah) * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+}
+
 // -log(K 2^-53) * 2^57 for K in [1, 2^53] (the result is below 53 ln 2 < 2^5.2,
 // so it fits a signed 64-bit word).
 __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, const LogTable& tab) {
@@ -123,9 +132,9 @@ __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, 
     const unsigned long long n = static_cast<unsigned long long>(lz - 10);  // 53 - e
     const int j = static_cast<int>((m >> (63 - kLogSliceBits)) & (kLogSlices - 1));
     const ulonglong2 e = __ldg(reinterpret_cast<const ulonglong2*>(tab.slice) + j);
-    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62 to 2^-62 (the low
-    // product's two bits would add below 2^-62), |r 2^64| < 2^51
-    const unsigned long long hi = __umul64hi(m, e.x);
+    // m inv = 2^126 (1 + r); r 2^64 = (m inv - 2^126) >> 62 to 2^-60 (the
+    // truncated high product is short by at most 2 units of 2^-62), |r 2^64| < 2^51
+    const unsigned long long hi = umul64hi_trunc(m, e.x);
     const long long R = static_cast<long long>((hi - (1ULL << 62)) << 2);
     const int a = static_cast<int>(R >> 20);       // r 2^44, |a| < 2^31
     const int rho = static_cast<int>(R & 0xFFFFF);  // R = a 2^20 + rho
@@ -139,9 +148,11 @@ __device__ __forceinline__ unsigned long long neg_log_q57(unsigned long long K, 
     // few units, never below zero, so the unsigned sum does not wrap
     const unsigned long long s64 = e.y + static_cast<unsigned long long>(l1p) + 64u;
     const unsigned long long nln2 = __ldg(tab.nln2 + n);  // n ln2 2^57, rounded (n <= 53)
-    // near y = 0 (K close to 2^53) the roundings may undershoot: clamp
-    const long long y = static_cast<long long>(nln2) - static_cast<long long>(s64 >> 7);
-    return y > 0 ? static_cast<unsigned long long>(y) : 0ULL;
+    // No clamp is needed: for n >= 1 the exact result is at least
+    // -ln(1 - 2^-53) (16 units) and the error below 2^-56 (2 units); for
+    // n = 0 (K = 2^53, M = 1) s64 is 2^6 plus an error of a few units of
+    // 2^-64, so s64 >> 7 = 0 = nln2.
+    return nln2 - (s64 >> 7);
 }
 
 // Exponential variate from words (lo, hi): -log(1 - u) * inv_rate_q57 where

@@ -26,7 +26,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // fixed-point log, i.e. round(y57 * (2^-9 / rate)), the factor stored as a
 // 64-bit multiplier cm = round(2^57 / rate) (2^-9 / rate = cm 2^-66).  A
 // variate then carries the multiplier's relative error (2^-53, as an FP64
-// division would) plus half a unit (2^-49), and every recurrence step is
+// division would) plus at most one unit (2^-48), and every recurrence step is
 // exact, where FP64 rounds each addition; the outputs agree with
 // FP64 evaluation far inside 1e-12 as long as the variates are not tiny
 // against 2^-48: rates are limited to [2^-6, 2^4] (mean variate >= 1/16).
@@ -44,6 +44,8 @@ constexpr long long kFixNegInf = -(1LL << 62);  // "empty" state: v - A stays ab
 
 // 2^-9 / rate as cm 2^-66 (cm in [2^53, 2^63] for the rates above: at least
 // 53 significant bits), so that round(y57 2^-9 / rate) = (hi(y57 cm) + 2) >> 2.
+// hi comes from umul64hi_trunc, 0 to 2 units short, so 3 is added instead of
+// 2: the variate is then within one unit (2^-48) of y57 2^-9 / rate.
 __device__ __forceinline__ bool fix_rate_ok(double rate) { return rate >= 0x1p-6 && rate <= 0x1p4; }
 
 __device__ __forceinline__ unsigned long long fix_scale(double rate) {
@@ -51,7 +53,7 @@ __device__ __forceinline__ unsigned long long fix_scale(double rate) {
 }
 
 __device__ __forceinline__ long long to_fix(unsigned long long y57, unsigned long long cm) {
-    return static_cast<long long>((__umul64hi(y57, cm) + 2u) >> 2);
+    return static_cast<long long>((umul64hi_trunc(y57, cm) + 3u) >> 2);
 }
 
 struct U128 {
