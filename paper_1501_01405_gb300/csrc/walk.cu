@@ -110,24 +110,30 @@ __device__ __forceinline__ bool walk_block(const uint4 b, int R, int& x, int& y,
 // This keeps the per-move work off the warp when one lane of 32 is near the
 // boundary, which (with stopping times spread over orders of magnitude) is
 // most of the time.  `live`: the lane has a walker; on return `done` marks
-// walkers that exited in this block (m = tau).
-__device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R, int& u, int& v, long long& m,
-                                                bool& done) {
+// walkers that exited in this block, `exit_at` (1..64) the exiting move
+// within it.
+//
+// The no-exit test: u's positions within the word lie between u - mu and
+// u - mu + 16 (mu its -1 steps), so with t = u - mu the word is safe in u iff
+// -R < t < R - 16, i.e. t + R - 1 in [0, 2R - 17): one unsigned compare
+// against lim = max(2R - 17, 0) (R <= 8: never safe).  The same for v.
+__device__ __forceinline__ uint32_t walk_safe_limit(int R) { return R > 8 ? static_cast<uint32_t>(2 * R - 17) : 0u; }
+
+__device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R, uint32_t lim, int& u, int& v,
+                                                int& exit_at, bool& done) {
     const int lane = threadIdx.x & 31;
     const uint32_t words[4] = {b.x, b.y, b.z, b.w};
     done = false;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t w = words[k];
-        const uint32_t b0 = w & kEven;
-        const uint32_t b01 = (w ^ (w >> 1)) & kEven;
-        const int mu = __popc(b0), mv = __popc(b01);  // -1 steps of u, of v
+        const int mu = __popc(w & kEven), mv = __popc((w ^ (w >> 1)) & kEven);  // -1 steps of u, of v
+        const int tu = u - mu, tv = v - mv;
         const bool going = live && !done;
-        const bool safe = u + (16 - mu) < R && u - mu > -R && v + (16 - mv) < R && v - mv > -R;
+        const bool safe = static_cast<uint32_t>(tu + (R - 1)) < lim && static_cast<uint32_t>(tv + (R - 1)) < lim;
         if (going && safe) {
-            u += 16 - 2 * mu;
-            v += 16 - 2 * mv;
-            m += 16;
+            u = tu + (16 - mu);
+            v = tv + (16 - mv);
         }
         unsigned near = __ballot_sync(kFull, going && !safe);
         while (near) {  // two walkers per pass: lanes 0..15 and 16..31
@@ -161,12 +167,11 @@ __device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R,
             if (me0 || me1) {
                 const unsigned h = me0 ? (hits & 0xFFFFu) : (hits >> 16);
                 if (h) {
-                    m += __ffs(h);
+                    exit_at = 16 * k + __ffs(h);
                     done = true;
                 } else {
                     u += me0 ? tu0 : tu1;
                     v += me0 ? tv0 : tv1;
-                    m += 16;
                 }
             }
         }
@@ -222,7 +227,8 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
     const unsigned below = (1u << lane) - 1u;
     bool active = false;
     int u = 0, v = 0, R = 1;
-    long long m = 0, out = 0;
+    uint32_t lim = 0, blk = 0;  // blk: Philox block index, the walker has made 64 blk moves
+    long long out = 0;
     uint32_t dp = 0, rep = 0, c3 = 0;
     long long next = 0, end = 0;  // warp-uniform range of the current chunk
     bool exhausted = false;       // warp-uniform
@@ -245,9 +251,10 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
             if (take) {
                 decode(job, g, R, dp, rep, out);
                 c3 = stream_word(0u, dp);
+                lim = walk_safe_limit(R);
                 u = 0;
                 v = 0;
-                m = 0;
+                blk = 0;
                 active = true;
             }
             const unsigned took = __ballot_sync(kFull, take);
@@ -255,11 +262,13 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
             need &= ~took;
         }
         if (!__any_sync(kFull, active)) break;
-        const uint4 b = philox(0u, static_cast<uint32_t>(m >> 6), rep, c3, rk);
+        const uint4 b = philox(0u, blk, rep, c3, rk);
         bool done;
-        walk_block_warp(b, active, R, u, v, m, done);
+        int exit_at = 0;
+        walk_block_warp(b, active, R, lim, u, v, exit_at, done);
         if (active) {
             if (done) {
+                const long long m = 64LL * blk + exit_at;
                 if (m > job.max_steps) {
                     job.tau[out] = -1;
                     atomicExch(job.err, 1);
@@ -267,10 +276,12 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
                     job.tau[out] = m;
                 }
                 active = false;
-            } else if (m >= job.max_steps) {
+            } else if (64LL * blk + 64 >= job.max_steps) {  // so blk stays below 2^32 (max_steps <= 2^38)
                 job.tau[out] = -1;
                 atomicExch(job.err, 1);
                 active = false;
+            } else {
+                ++blk;
             }
         }
     }
