@@ -44,6 +44,7 @@ struct WalkJob {
     long long total;
     long long max_steps;
     long long chunk;
+    unsigned long long reps_magic;  // ceil(2^64 / n_reps) for n_reps >= 2 (0 for n_reps = 1)
     int64_t* tau;
     unsigned long long* ticket;
     int* err;
@@ -178,9 +179,16 @@ __device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R,
     }
 }
 
+// g div n_reps without a 64-bit division: hi(g * ceil(2^64 / n_reps)) exceeds
+// g / n_reps by less than g / 2^64 < 1, so it is the quotient or one more,
+// which the remainder's sign tells.
 __device__ __forceinline__ void decode(const WalkJob& job, long long g, int& R, uint32_t& dp,
                                        uint32_t& rep, long long& out) {
-    const long long k = g / job.n_reps;
+    long long k = g;
+    if (job.reps_magic) {
+        k = static_cast<long long>(__umul64hi(static_cast<unsigned long long>(g), job.reps_magic));
+        if (g - k * job.n_reps < 0) --k;
+    }
     rep = static_cast<uint32_t>(g - k * job.n_reps);
     R = job.radius[k];
     dp = static_cast<uint32_t>(job.dp_of[k]);
@@ -340,6 +348,12 @@ __global__ void walk_warp_coop_kernel(WalkJob job, const __grid_constant__ Round
     }
 }
 
+// ceil(2^64 / n) for n >= 2, 0 for n = 1 (WalkJob::reps_magic).
+unsigned long long reps_reciprocal(long long n) {
+    if (n < 2) return 0ull;
+    return static_cast<unsigned long long>(((static_cast<unsigned __int128>(1) << 64) + n - 1) / n);
+}
+
 }  // namespace
 
 // Launch on device-resident (radius, dp) tables in processing order.
@@ -354,6 +368,7 @@ mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_p
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
     job.chunk = chunk > 0 ? chunk : 16;
+    job.reps_magic = reps_reciprocal(n_reps);
     job.tau = d_tau;
     job.ticket = d_ticket;
     job.err = device_error_flags();
@@ -506,6 +521,7 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
     job.chunk = chunk > 0 ? chunk : 16;
+    job.reps_magic = reps_reciprocal(n_reps);
     job.tau = d_tau;
     job.ticket = reinterpret_cast<unsigned long long*>(base);
     job.err = reinterpret_cast<int*>(base + 8);
