@@ -302,10 +302,10 @@ __global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __
         double wa = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
         bool overflow = false;
         // client n's four log values; then one step of the recurrence
-        auto logs = [&](long long n, unsigned long long& ya, unsigned long long& y1, unsigned long long& y2,
+        auto logs = [&](uint32_t n, unsigned long long& ya, unsigned long long& y1, unsigned long long& y2,
                         unsigned long long& y3) {
-            const uint4 b0 = philox(0u, static_cast<uint32_t>(n), rep, c3, rk);
-            const uint4 b1 = philox(1u, static_cast<uint32_t>(n), rep, c3, rk);
+            const uint4 b0 = philox(0u, n, rep, c3, rk);
+            const uint4 b1 = philox(1u, n, rep, c3, rk);
             ya = neg_log_q57(word_k(b0.x, b0.y), tab);
             y1 = neg_log_q57(word_k(b0.z, b0.w), tab);
             y2 = neg_log_q57(word_k(b1.x, b1.y), tab);
@@ -324,9 +324,11 @@ __global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __
             return v3 < kFixGuard;
         };
         // the early window also sums the same variates as doubles (expo_fast);
-        // the loop after it carries none of that state
-        long long n = 0;
-        for (; n < w_len; ++n) {
+        // the loop after it carries none of that state.  Client indices are
+        // 32-bit (n_clients < 2^32, the counter word c1).
+        const uint32_t nc = static_cast<uint32_t>(n_clients), nw = static_cast<uint32_t>(w_len);
+        uint32_t n = 0;
+        for (; n < nw; ++n) {
             unsigned long long ya, y1, y2, y3;
             logs(n, ya, y1, y2, y3);
             wa += __ull2double_rn(ya) * i_lam;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(128, 8) tandem3_serial_kernel(const double* __
                 break;
             }
         }
-        for (; !overflow && n < n_clients; ++n) {
+        for (; !overflow && n < nc; ++n) {
             unsigned long long ya, y1, y2, y3;
             logs(n, ya, y1, y2, y3);
             if (!step(ya, y1, y2, y3)) overflow = true;
