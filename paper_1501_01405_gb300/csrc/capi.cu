@@ -327,9 +327,9 @@ std::vector<Plan> candidates(int kind) {
             break;
         case MRIP_FOREST_FIRE: add(MRIP_MAP_CTA, 0, 0, 0); break;
         case MRIP_WALK_L1_EXIT:
-            for (int w : {4, 8, 16})
-                for (int k : {2, 4, 8})
-                    for (int ch : {32, 128}) add(MRIP_MAP_PERSISTENT, w, k, ch);
+            for (int w : {8, 16, 32})
+                for (int k : {1, 2, 4})
+                    for (int ch : {16, 64}) add(MRIP_MAP_PERSISTENT, w, k, ch);
             add(MRIP_MAP_THREAD, 0, 0, 0);
             add(MRIP_MAP_WARP_COOP, 0, 0, 0);
             add(MRIP_MAP_WARP_1LANE, 0, 0, 0);

@@ -179,6 +179,66 @@ __device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R,
     }
 }
 
+// Tail of the persistent mapping: once no replications are left to take and
+// at most kTailLanes lanes of a warp still walk, the warp finishes those
+// walkers one at a time, all 32 lanes on one walker.  Per round the walker
+// advances 512 moves: lane l takes word l mod 4 of block blk + l div 4 (the
+// four lanes of a block compute it alike), a warp scan of the words' u and v
+// displacements gives each word's start, a word that may reach the boundary
+// is stepped move by move, and a ballot picks the first exit.  In the
+// lane-parallel loop a walker makes 64 moves per warp round, so the longest
+// walkers (the exit time has an exponential tail) would otherwise set the
+// launch's length.
+constexpr int kTailLanes = 16;
+
+// Whole walk from (u, v) after blk blocks; returns tau, or -1 past max_steps.
+// Warp-uniform arguments; every lane returns the same value.
+__device__ long long walk_tail_coop(int u, int v, uint32_t blk, int R, uint32_t lim, uint32_t rep, uint32_t c3,
+                                    long long max_steps, const RoundKeys& rk) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        const uint4 b = philox(0u, blk + static_cast<uint32_t>(lane >> 2), rep, c3, rk);
+        const int sel = lane & 3;
+        const uint32_t w = sel == 0 ? b.x : sel == 1 ? b.y : sel == 2 ? b.z : b.w;
+        const int mu = __popc(w & kEven), mv = __popc((w ^ (w >> 1)) & kEven);
+        const int du = 16 - 2 * mu, dv = 16 - 2 * mv;
+        int su = du, sv = dv;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int pu = __shfl_up_sync(kFull, su, off), pv = __shfl_up_sync(kFull, sv, off);
+            if (lane >= off) {
+                su += pu;
+                sv += pv;
+            }
+        }
+        int pu = u + su - du, pv = v + sv - dv;  // position before this lane's word
+        int e = 0;
+        const bool safe = static_cast<uint32_t>(pu - mu + (R - 1)) < lim &&
+                          static_cast<uint32_t>(pv - mv + (R - 1)) < lim;
+        if (!safe) {
+            for (int s = 0; s < 16; ++s) {
+                const uint32_t f = (w >> (2 * s)) & 3u;
+                pu += (f & 1u) ? -1 : 1;
+                pv += ((f ^ (f >> 1)) & 1u) ? -1 : 1;
+                if (max(abs(pu), abs(pv)) >= R) {
+                    e = s + 1;
+                    break;
+                }
+            }
+        }
+        const unsigned ex = __ballot_sync(kFull, e != 0);
+        if (ex) {
+            const int first = __ffs(ex) - 1;
+            const long long tau = 64LL * blk + 16 * first + __shfl_sync(kFull, e, first);
+            return tau > max_steps ? -1 : tau;
+        }
+        if (64LL * blk + 512 >= max_steps) return -1;  // also keeps blk + 8 below 2^32
+        u += __shfl_sync(kFull, su, 31);
+        v += __shfl_sync(kFull, sv, 31);
+        blk += 8;
+    }
+}
+
 // g div n_reps without a 64-bit division: hi(g * ceil(2^64 / n_reps)) exceeds
 // g / n_reps by less than g / 2^64 < 1, so it is the quotient or one more,
 // which the remainder's sign tells.
@@ -269,7 +329,22 @@ __global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ Roun
             next += __popc(took);
             need &= ~took;
         }
-        if (!__any_sync(kFull, active)) break;
+        const unsigned act = __ballot_sync(kFull, active);
+        if (!act) break;
+        if (exhausted && __popc(act) <= kTailLanes) {
+            for (unsigned rest = act; rest; rest &= rest - 1) {
+                const int src = __ffs(rest) - 1;
+                const long long tau = walk_tail_coop(
+                    __shfl_sync(kFull, u, src), __shfl_sync(kFull, v, src), __shfl_sync(kFull, blk, src),
+                    __shfl_sync(kFull, R, src), __shfl_sync(kFull, lim, src), __shfl_sync(kFull, rep, src),
+                    __shfl_sync(kFull, c3, src), job.max_steps, rk);
+                if (lane == src) {
+                    job.tau[out] = tau;
+                    if (tau < 0) atomicExch(job.err, 1);
+                }
+            }
+            break;
+        }
         const uint4 b = philox(0u, blk, rep, c3, rk);
         bool done;
         int exit_at = 0;
@@ -376,8 +451,8 @@ mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_p
     const RoundKeys rk = expand_key(seed);
     if (job.total == 0) return MRIP_OK;
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_PERSISTENT) {
-        const int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
-        const int cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
+        const int wpc = warps_per_cta > 0 ? warps_per_cta : 32;  // one CTA of 32 warps per SM
+        const int cps = ctas_per_sm > 0 ? ctas_per_sm : 1;
         if (wpc > 32 || cps > 64) return fail(MRIP_EINVAL, "walk: warps_per_cta <= 32, ctas_per_sm <= 64");
         if (!d_ticket) return fail(MRIP_EINVAL, "walk: persistent mapping needs a ticket counter");
         cudaError_t e = cudaMemsetAsync(d_ticket, 0, sizeof(unsigned long long), st);
@@ -494,8 +569,8 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     if (mapping != MRIP_MAP_AUTO && mapping != MRIP_MAP_PERSISTENT && mapping != MRIP_MAP_THREAD &&
         mapping != MRIP_MAP_WARP_1LANE && mapping != MRIP_MAP_WARP_COOP)
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: unknown mapping");
-    const int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
-    const int cps = ctas_per_sm > 0 ? ctas_per_sm : 4;
+    const int wpc = warps_per_cta > 0 ? warps_per_cta : 32;
+    const int cps = ctas_per_sm > 0 ? ctas_per_sm : 1;
     if (wpc > 32 || cps > 64)
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: warps_per_cta <= 32, ctas_per_sm <= 64");
 
