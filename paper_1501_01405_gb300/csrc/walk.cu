@@ -17,7 +17,10 @@
 //               walker exits, so lanes stay busy despite uneven lengths;
 //               words that may cross the boundary are walked by the whole
 //               warp (walk_block_warp), so one lane near the boundary does
-//               not serialise the other 31.
+//               not serialise the other 31; when the ticket runs out, a
+//               warp finishes its last walkers with all 32 lanes on one
+//               walker at a time (walk_tail_coop).  Default launch: one CTA
+//               of 32 warps per SM, chunks of 16.
 //   THREAD      one replication per thread (TLP), no refill.
 //   WARP_1LANE  one replication per warp, lane 0 only (the paper's WLP).
 //   WARP_COOP   one replication per warp: the 32 lanes take 32 consecutive
