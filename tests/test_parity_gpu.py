@@ -370,6 +370,28 @@ def test_walk_step_cap_reported(eng, torch_mod, mapping):
     eng.mrip_check_device_flags()  # the flag was cleared
 
 
+@pytest.mark.parametrize("shape", [(1, 1, 64), (0, 0, 0)])
+def test_walk_step_cap_inside_rounds(eng, torch_mod, shape):
+    """Exit times around the cap (E[tau] ~ 960 at R = 40, cap 1,000, not a
+    multiple of 64 or 512): walkers exit before, at and after it, in the
+    lane-parallel loop (one warp per SM takes 64 at a time, so lanes refill)
+    and in the cooperative tail (512-move rounds). Bit-exact, -1 past the cap."""
+    t = torch_mod
+    radii, n_reps, cap = [40.0, 41.0], 3000, 1000
+    tau = t.empty(len(radii) * n_reps, dtype=t.int64, device="cuda")
+    w, k, ch = shape
+    eng.mrip_walk_simulate(radii, n_reps, 5, cap, eng.MRIP_MAP_PERSISTENT, tau,
+                           warps_per_cta=w, ctas_per_sm=k, chunk=ch)
+    t.cuda.synchronize()
+    with pytest.raises(eng.MripError) as e:
+        eng.mrip_check_device_flags()
+    assert e.value.code == 4
+    got = tau.cpu().numpy()
+    ref = oracle.walk(radii, *oracle.all_items(len(radii), n_reps), 5, max_steps=cap, threads=threads())
+    assert np.array_equal(got, ref)
+    assert np.any(got == -1) and np.any(got > 900)
+
+
 def test_walk_workload_full_sampled(eng, torch_mod):
     """8 radii x 2^17 replications, persistent work stealing; 1,600 sampled
     replications bit-exact, every tau has the parity of R."""
