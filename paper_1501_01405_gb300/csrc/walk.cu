@@ -19,8 +19,9 @@
 //               warp (walk_block_warp), so one lane near the boundary does
 //               not serialise the other 31; when the ticket runs out, a
 //               warp finishes its last walkers with all 32 lanes on one
-//               walker at a time (walk_tail_coop).  Default launch: one CTA
-//               of 32 warps per SM, chunks of 16.
+//               walker at a time (walk_tail_coop, 2,048 moves per
+//               round).  Default launch: one CTA of 32 warps per SM,
+//               chunks of 16.
 //   THREAD      one replication per thread (TLP), no refill.
 //   WARP_1LANE  one replication per warp, lane 0 only (the paper's WLP).
 //   WARP_COOP   one replication per warp: the 32 lanes take 32 consecutive
@@ -185,13 +186,12 @@ __device__ __forceinline__ void walk_block_warp(const uint4 b, bool live, int R,
 // Tail of the persistent mapping: once no replications are left to take and
 // at most kTailLanes lanes of a warp still walk, the warp finishes those
 // walkers one at a time, all 32 lanes on one walker.  Per round the walker
-// advances 512 moves: lane l takes word l mod 4 of block blk + l div 4 (the
-// four lanes of a block compute it alike), a warp scan of the words' u and v
-// displacements gives each word's start, a word that may reach the boundary
-// is stepped move by move, and a ballot picks the first exit.  In the
-// lane-parallel loop a walker makes 64 moves per warp round, so the longest
-// walkers (the exit time has an exponential tail) would otherwise set the
-// launch's length.
+// advances 2,048 moves: lane l takes block blk + l (64 moves), a warp scan of
+// the blocks' u and v displacements gives each block's start, a block that
+// may reach the boundary is taken word by word (a word that may reach it
+// move by move), and a ballot picks the first exit.  In the lane-parallel
+// loop a walker makes 64 moves per warp round, so the longest walkers (the
+// exit time has an exponential tail) would otherwise set the launch's length.
 constexpr int kTailLanes = 16;
 
 // Whole walk from (u, v) after blk blocks; returns tau, or -1 past max_steps.
@@ -199,12 +199,18 @@ constexpr int kTailLanes = 16;
 __device__ long long walk_tail_coop(int u, int v, uint32_t blk, int R, uint32_t lim, uint32_t rep, uint32_t c3,
                                     long long max_steps, const RoundKeys& rk) {
     const int lane = threadIdx.x & 31;
+    // the same no-exit test as walk_block_warp, over 64 moves: t + R - 1 in [0, 2R - 65)
+    const uint32_t lim64 = R > 32 ? static_cast<uint32_t>(2 * R - 65) : 0u;
     while (true) {
-        const uint4 b = philox(0u, blk + static_cast<uint32_t>(lane >> 2), rep, c3, rk);
-        const int sel = lane & 3;
-        const uint32_t w = sel == 0 ? b.x : sel == 1 ? b.y : sel == 2 ? b.z : b.w;
-        const int mu = __popc(w & kEven), mv = __popc((w ^ (w >> 1)) & kEven);
-        const int du = 16 - 2 * mu, dv = 16 - 2 * mv;
+        const uint4 b = philox(0u, blk + static_cast<uint32_t>(lane), rep, c3, rk);
+        const uint32_t words[4] = {b.x, b.y, b.z, b.w};
+        int mu = 0, mv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mu += __popc(words[k] & kEven);
+            mv += __popc((words[k] ^ (words[k] >> 1)) & kEven);
+        }
+        const int du = 64 - 2 * mu, dv = 64 - 2 * mv;
         int su = du, sv = dv;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -214,31 +220,41 @@ __device__ long long walk_tail_coop(int u, int v, uint32_t blk, int R, uint32_t 
                 sv += pv;
             }
         }
-        int pu = u + su - du, pv = v + sv - dv;  // position before this lane's word
+        int pu = u + su - du, pv = v + sv - dv;  // position before this lane's block
         int e = 0;
-        const bool safe = static_cast<uint32_t>(pu - mu + (R - 1)) < lim &&
-                          static_cast<uint32_t>(pv - mv + (R - 1)) < lim;
-        if (!safe) {
-            for (int s = 0; s < 16; ++s) {
-                const uint32_t f = (w >> (2 * s)) & 3u;
-                pu += (f & 1u) ? -1 : 1;
-                pv += ((f ^ (f >> 1)) & 1u) ? -1 : 1;
-                if (max(abs(pu), abs(pv)) >= R) {
-                    e = s + 1;
-                    break;
+        if (!(static_cast<uint32_t>(pu - mu + (R - 1)) < lim64 && static_cast<uint32_t>(pv - mv + (R - 1)) < lim64)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e) break;
+                const uint32_t w = words[k];
+                const int wu = __popc(w & kEven), wv = __popc((w ^ (w >> 1)) & kEven);
+                if (static_cast<uint32_t>(pu - wu + (R - 1)) < lim && static_cast<uint32_t>(pv - wv + (R - 1)) < lim) {
+                    pu += 16 - 2 * wu;
+                    pv += 16 - 2 * wv;
+                    continue;
+                }
+                for (int s = 0; s < 16; ++s) {
+                    const uint32_t f = (w >> (2 * s)) & 3u;
+                    pu += (f & 1u) ? -1 : 1;
+                    pv += ((f ^ (f >> 1)) & 1u) ? -1 : 1;
+                    if (max(abs(pu), abs(pv)) >= R) {
+                        e = 16 * k + s + 1;
+                        break;
+                    }
                 }
             }
         }
         const unsigned ex = __ballot_sync(kFull, e != 0);
         if (ex) {
             const int first = __ffs(ex) - 1;
-            const long long tau = 64LL * blk + 16 * first + __shfl_sync(kFull, e, first);
+            const long long tau = 64LL * (static_cast<long long>(blk) + first) + __shfl_sync(kFull, e, first);
             return tau > max_steps ? -1 : tau;
         }
-        if (64LL * blk + 512 >= max_steps) return -1;  // also keeps blk + 8 below 2^32
+        // blocks past the cap are never used (and blk + 32 stays below 2^32)
+        if (64LL * blk + 2048 >= max_steps) return -1;
         u += __shfl_sync(kFull, su, 31);
         v += __shfl_sync(kFull, sv, 31);
-        blk += 8;
+        blk += 32;
     }
 }
 
@@ -293,7 +309,7 @@ __global__ void walk_serial_kernel(WalkJob job, const __grid_constant__ RoundKey
     walk_serial(job, g, rk);
 }
 
-__global__ void walk_persistent_kernel(WalkJob job, const __grid_constant__ RoundKeys rk) {
+__global__ void __launch_bounds__(1024) walk_persistent_kernel(WalkJob job, const __grid_constant__ RoundKeys rk) {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     bool active = false;
