@@ -292,7 +292,9 @@ mrip_status mrip_forest_fire_skip_simulate(const double *d_dps, int32_t n_dp, in
  * device int64 n_dp * n_reps (-1 where max_steps was reached, and the call's
  * later status check reports MRIP_ESTEPCAP).  mapping: THREAD, WARP_1LANE,
  * WARP_COOP or PERSISTENT (AUTO = PERSISTENT); warps_per_cta, ctas_per_sm and
- * chunk (replications per ticket) shape PERSISTENT (0 = default). */
+ * chunk (replications per ticket) shape PERSISTENT (0 = default: 32 warps,
+ * one CTA per SM, chunks of 16; when no replications are left, a warp
+ * finishes its last walkers with all 32 lanes on one walker at a time). */
 mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t n_reps,
                                uint64_t seed, int64_t max_steps, int mapping,
                                int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk,
