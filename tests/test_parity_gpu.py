@@ -211,9 +211,10 @@ def test_tandem_warp_coop_ragged(eng, torch_mod, n_clients, window, mapping):
     np.testing.assert_allclose(f.cpu().numpy().reshape(8, -1).T, rf, rtol=REL)
 
 
-def test_tandem_workload_full_sampled(eng, torch_mod):
+def test_tandem_workload_full(eng, torch_mod):
     """4,096 design points x 256 replications x 10,000 clients on the GPU;
-    96 sampled replications against the oracle."""
+    every replication's output and 8 features against the oracle (about 40 s
+    on 16 host cores)."""
     t = torch_mod
     w = mrip_inputs.workload("tandem_cv")
     n = w["n_dp"] * w["n_reps"]
@@ -221,13 +222,10 @@ def test_tandem_workload_full_sampled(eng, torch_mod):
     f = t.empty(8 * n, dtype=t.float64, device="cuda")
     eng.mrip_tandem3_simulate(dev(t, w["dps"]), 0, w["n_reps"], w["n_clients"], w["window"],
                               w["seed"], 0, eng.MRIP_MAP_THREAD, y, f)
-    rng = np.random.default_rng(9)
-    pick = np.concatenate([[0, n - 1, 255, 256], rng.choice(n, 92, replace=False)])
-    dp, rep = pick // w["n_reps"], pick % w["n_reps"]
-    ry, rf = oracle.tandem3(w["dps"], dp, rep, w["n_clients"], w["seed"], window=w["window"],
-                            threads=threads())
-    gy = y.cpu().numpy()[pick]
-    gf = f.cpu().numpy().reshape(8, -1)[:, pick].T
+    ry, rf = oracle.tandem3(w["dps"], *oracle.all_items(w["n_dp"], w["n_reps"]), w["n_clients"], w["seed"],
+                            window=w["window"], threads=threads())
+    gy = y.cpu().numpy()
+    gf = f.cpu().numpy().reshape(8, -1).T
     np.testing.assert_allclose(gy, ry, rtol=REL)
     np.testing.assert_allclose(gf, rf, rtol=REL)
 
@@ -286,19 +284,18 @@ def test_forest_fire_zero_steps_is_initial_state(eng, torch_mod):
         assert np.array_equal(final.cpu().numpy().reshape(2, L, L)[r], rs)
 
 
-def test_forest_fire_workload_full_sampled(eng, torch_mod):
-    """128x128, 1,000 steps, 1,024 replications on the GPU; four replications
-    (first, last, two inside) bit-exact against the oracle."""
+def test_forest_fire_workload_full(eng, torch_mod):
+    """128x128, 1,000 steps, 1,024 replications on the GPU; every replication's
+    1,000 counts bit-exact against the oracle (about 7 s on 16 host cores)."""
     t = torch_mod
     w = mrip_inputs.workload("ff128")
     counts = t.empty(w["n_reps"] * w["n_steps"], dtype=t.int32, device="cuda")
     eng.mrip_forest_fire_simulate(dev(t, w["dps"]), w["n_reps"], w["L"], w["n_steps"],
                                   w["density"], w["seed"], None, counts)
     gc = counts.cpu().numpy().reshape(w["n_reps"], w["n_steps"])
-    pick = np.array([0, 1, 511, 1023])
     rc = oracle.forest_fire(w["L"], w["n_steps"], w["dps"], w["density"],
-                            np.zeros(4, np.int32), pick, w["seed"], threads=threads())
-    assert np.array_equal(gc[pick], rc)
+                            *oracle.all_items(1, w["n_reps"]), w["seed"], threads=threads())
+    assert np.array_equal(gc, rc)
     assert gc.min() >= 0 and gc.max() <= w["L"] ** 2
 
 
@@ -392,9 +389,10 @@ def test_walk_step_cap_inside_rounds(eng, torch_mod, shape):
     assert np.any(got == -1) and np.any(got > 900)
 
 
-def test_walk_workload_full_sampled(eng, torch_mod):
-    """8 radii x 2^17 replications, persistent work stealing; 1,600 sampled
-    replications bit-exact, every tau has the parity of R."""
+def test_walk_workload_full(eng, torch_mod):
+    """8 radii x 2^17 replications, persistent work stealing in the bench's
+    launch; every replication bit-exact against the oracle (about 3 s on 16
+    host cores), every tau has the parity of R."""
     t = torch_mod
     w = mrip_inputs.workload("walk8")
     radii = w["dps"][:, 0]
@@ -406,10 +404,8 @@ def test_walk_workload_full_sampled(eng, torch_mod):
     g = tau.cpu().numpy()
     dp = np.repeat(np.arange(len(radii)), w["n_reps"])
     assert np.all(g % 2 == radii[dp].astype(np.int64) % 2) and np.all(g >= radii[dp])
-    rng = np.random.default_rng(11)
-    pick = np.concatenate([np.arange(8) * w["n_reps"], rng.choice(n, 1592, replace=False)])
-    ref = oracle.walk(radii, pick // w["n_reps"], pick % w["n_reps"], w["seed"], threads=threads())
-    assert np.array_equal(g[pick], ref)
+    ref = oracle.walk(radii, *oracle.all_items(len(radii), w["n_reps"]), w["seed"], threads=threads())
+    assert np.array_equal(g, ref)
 
 
 # ------------------------------------------------------------------ statistics
