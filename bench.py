@@ -806,8 +806,8 @@ def reference_arm(args, wl, rank, world):
         return
     threads = oracle.host_threads()
     oracle.lib()
-    # size each step so the whole run stays within about three minutes
-    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    # size each step so the whole run stays within about three minutes (--ref-seconds)
+    per_step = max(0.2, min(8.0, args.ref_seconds / max(1, args.steps + args.warmup)))
     n_cal = threads
     t0 = time.perf_counter()
     wl.oracle_sample(n_cal, threads)
@@ -914,6 +914,8 @@ def main():
                     help="profiling only: keep the first N design points (tandem) or use N "
                          "replications per design point (other workloads)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: host seconds for the whole run (each step 0.2 .. 8 s)")
     ap.add_argument("--no-cv", action="store_true",
                     help="skip the plain-vs-control-variate time-to-target measurement")
     args = ap.parse_args()

@@ -4,7 +4,9 @@ Integer and lattice outputs must match bit for bit; FP64 outputs within
 1e-12 relative (the engine's log may differ from the C library's by an ulp,
 and a warp-cooperative replay sums in another order).  Sizes span several
 tiles with ragged tails; the full-size workloads run on the GPU in the
-launch configuration the bench uses and are checked on sampled replications.
+launch configuration the bench uses and are checked on every replication
+(M/M/1, forest fire 128^2, walk batch, tandem) or on sampled ones (the
+256^2 forest fire, the skip-sampled variant).
 """
 import math
 
