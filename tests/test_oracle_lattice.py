@@ -189,6 +189,47 @@ def test_walk_exact_distribution_small_radius(R):
     assert abs(tau.mean() - mean_exact) < 5 * math.sqrt(np.var(tau) / n)
 
 
+def _exit_survival_1d(R, kmax):
+    """P(T > k), k = 0..kmax, for a +-1 walk from 0 and T the first k with
+    |position| >= R (dynamic programming over the 2R - 1 inner sites)."""
+    p = np.zeros(2 * R - 1)
+    p[R - 1] = 1.0
+    surv = np.empty(kmax + 1)
+    surv[0] = 1.0
+    for k in range(1, kmax + 1):
+        q = np.zeros_like(p)
+        q[1:] += 0.5 * p[:-1]
+        q[:-1] += 0.5 * p[1:]
+        p = q
+        surv[k] = p.sum()
+    return surv
+
+
+@pytest.mark.parametrize("R", [16, 33])
+def test_walk_exact_distribution_by_diagonal_coordinates(R):
+    """In u = x + y, v = x - y a move steps u and v by independent fair +-1
+    (u's sign is bit 0, v's the xor of the two bits) and |x| + |y| >= R iff
+    max(|u|, |v|) >= R, so P(tau > k) = P(T > k)^2 with T the exit time of a
+    1-D walk from (-R, R): an exact law at the radii the GPU tests use,
+    derived independently of the 2-D dynamic programming above."""
+    n = 20000
+    tau = oracle.walk([float(R)], np.zeros(n, np.int32), np.arange(n), 7)
+    kmax = int(tau.max()) + 40 * R * R
+    surv = _exit_survival_1d(R, kmax) ** 2
+    p = np.append(surv[:-1] - surv[1:], surv[-1])  # P(tau = k), k = 1..kmax, then the rest
+    # bins of roughly equal probability along the exact CDF
+    cdf = np.cumsum(p)
+    edges = np.searchsorted(cdf, np.linspace(0, 1, 41)[1:-1]) + 1
+    edges = np.unique(np.concatenate([[1], edges, [kmax + 1]]))
+    ex = np.array([p[lo - 1:hi - 1].sum() for lo, hi in zip(edges[:-1], edges[1:])]) * n
+    obs = np.array([np.count_nonzero((tau >= lo) & (tau < hi)) for lo, hi in zip(edges[:-1], edges[1:])])
+    ex[-1] += n * p[kmax:].sum()
+    assert np.all(ex >= 5) and obs.sum() == n
+    assert stats.chisquare(obs, ex * n / ex.sum()).pvalue > 1e-4
+    mean_exact = float(surv[:-1].sum())  # E[tau] = sum_k P(tau > k)
+    assert abs(tau.mean() - mean_exact) < 5 * math.sqrt(np.var(tau) / n)
+
+
 def test_walk_parity_large_radius_and_cap():
     radii = [16.0, 33.0]
     dp = np.repeat(np.arange(2, dtype=np.int32), 300)
