@@ -143,6 +143,19 @@ mrip_status mrip_set_stream(mrip_model *model, void *cuda_stream);
 mrip_status mrip_run(mrip_model *model, const double *design_points, int32_t n_dp,
                      int64_t n_reps, uint64_t seed);
 
+/* Replications rep_lo .. rep_hi - 1 of every design point: the shard of one
+ * experiment that one GPU (or one process) runs when the replications of
+ * an experimental plan are split (paper, Section 1: replications are
+ * independent).  Every replication is a function of (seed, design point,
+ * replication index) alone, so the shards of any partition of 0 .. n - 1
+ * give exactly the per-replication outputs of one mrip_run of n; their
+ * (n, mean, M2) triples (mrip_moments) merge with mrip_stats_merge.
+ * Outputs have rep_hi - rep_lo columns per design point; otherwise as
+ * mrip_run (which is mrip_run_range(model, dps, n_dp, 0, n_reps, seed)).
+ * 0 <= rep_lo < rep_hi <= 2^32. */
+mrip_status mrip_run_range(mrip_model *model, const double *design_points, int32_t n_dp,
+                           int64_t rep_lo, int64_t rep_hi, uint64_t seed);
+
 /* Same as mrip_run with design_points already on the device. */
 mrip_status mrip_run_device(mrip_model *model, const double *d_design_points, int32_t n_dp,
                             int64_t n_reps, uint64_t seed);
@@ -152,6 +165,12 @@ mrip_status mrip_run_device(mrip_model *model, const double *d_design_points, in
  * MRIP_ESTEPCAP if a replication hit its step cap, MRIP_ESTATE before any
  * run. */
 mrip_status mrip_stats(mrip_model *model, double conf, mrip_stat *out);
+
+/* Synchronous.  The last run's per-design-point (n, mean, M2) triples
+ * (Welford/Chan, FP64) into the caller's host array nmm2_out[n_dp][3]: the
+ * exact input of mrip_stats_merge when shards of one experiment are
+ * combined.  Errors as mrip_stats. */
+mrip_status mrip_moments(mrip_model *model, double *nmm2_out);
 
 /* Synchronous.  Copy output plane `which` of the last run into dst
  * (dst_bytes must be at least its size; on_device != 0: dst is a device
@@ -221,7 +240,9 @@ mrip_status mrip_expo(const uint32_t *d_lo, const uint32_t *d_hi, const double *
                       int64_t n, double *d_u, double *d_e, void *stream);
 
 /* M/M/1 replications (paper, Section 5.1, second model).  d_dps: device
- * n_dp x 2 (lambda, mu).  Client n uses block (c0 = 0, c1 = n): words 0,1 ->
+ * n_dp x 2 (lambda, mu).  Replications rep0 .. rep0 + n_reps - 1 (indices
+ * < 2^32; output column r is replication rep0 + r).  Client n uses block
+ * (c0 = 0, c1 = n): words 0,1 ->
  * service S_n ~ Exp(mu), words 2,3 -> gap A_{n+1} ~ Exp(lambda); W_0 = 0,
  * W_{n+1} = max(0, W_n + S_n - A_{n+1}).  Outputs (device, n_dp * n_reps,
  * any may be NULL): mean wait W, mean idle max(0, A_{n+1} - W_n - S_n),
@@ -229,7 +250,7 @@ mrip_status mrip_expo(const uint32_t *d_lo, const uint32_t *d_hi, const double *
  * WARP_1LANE, WARP_COOP or CTA (one replication per CTA of up to 1,024
  * threads, ~4 clients each, block scan of the maps; for a few replications
  * whose latency matters).  AUTO = THREAD. */
-mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+mrip_status mrip_mm1_simulate(const double *d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                               int64_t n_clients, uint64_t seed, int mapping,
                               double *d_wait, double *d_idle, double *d_system, void *stream);
 
@@ -253,7 +274,9 @@ mrip_status mrip_tandem3_simulate(const double *d_dps, int32_t n_dp, int64_t rep
 
 /* Forest-fire automaton, one CTA per replication, lattice bit-packed in
  * registers and shared memory.  d_dps: device n_dp x 2 (p_grow,
- * p_lightning).  L multiple of 32 in 32..512, n_steps >= 0.
+ * p_lightning).  Replications rep0 .. rep0 + n_reps - 1 (indices < 2^32;
+ * output row r is replication rep0 + r).  L multiple of 32 in 32..512,
+ * n_steps >= 0.
  * Initial state from tag 1 (tree iff word < floor(density 2^32)), or from
  * d_init (device uint8 L*L per replication, states 0/1/2; may be NULL).
  * Step t uses word (i mod 4) of block (i div 4, t) for cell i = y L + x:
@@ -262,7 +285,7 @@ mrip_status mrip_tandem3_simulate(const double *d_dps, int32_t n_dp, int64_t rep
  * 2^32).  Outputs (device, may be NULL): d_counts int32 [n_dp*n_reps][n_steps]
  * burning cells after each step; d_scalar double [n_dp*n_reps] =
  * sum_t counts / (n_steps L^2); d_final uint8 [n_dp*n_reps][L*L]. */
-mrip_status mrip_forest_fire_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+mrip_status mrip_forest_fire_simulate(const double *d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                       int32_t L, int32_t n_steps, double density,
                                       uint64_t seed, const uint8_t *d_init,
                                       int32_t *d_counts, double *d_scalar, uint8_t *d_final,
@@ -280,7 +303,7 @@ mrip_status mrip_forest_fire_simulate(const double *d_dps, int32_t n_dp, int64_t
  * event.  Per cell and step the law is the per-cell model's with the exact
  * probabilities; the work per step is p L^2 variates instead of L^2 words.
  * p <= 0 (or NaN): no events; p >= 1: every cell. */
-mrip_status mrip_forest_fire_skip_simulate(const double *d_dps, int32_t n_dp, int64_t n_reps,
+mrip_status mrip_forest_fire_skip_simulate(const double *d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                            int32_t L, int32_t n_steps, double density,
                                            uint64_t seed, const uint8_t *d_init, int32_t *d_counts,
                                            double *d_scalar, uint8_t *d_final, void *stream);
@@ -288,14 +311,16 @@ mrip_status mrip_forest_fire_skip_simulate(const double *d_dps, int32_t n_dp, in
 /* L1-exit walk: simple random walk on Z^2 from the origin; move m reads the
  * 2-bit field k = m mod 64 of block (0, m div 64): word k div 16, bits
  * 2(k mod 16)..+1; 0:+x 1:-x 2:+y 3:-y.  tau = moves made when |x|+|y|
- * first reaches R.  radii: HOST array n_dp (integers 1..65536).  d_tau:
+ * first reaches R.  Replications rep0 .. rep0 + n_reps - 1 (indices < 2^32;
+ * output column r is replication rep0 + r).  radii: HOST array n_dp
+ * (integers 1..65536).  d_tau:
  * device int64 n_dp * n_reps (-1 where max_steps was reached, and the call's
  * later status check reports MRIP_ESTEPCAP).  mapping: THREAD, WARP_1LANE,
  * WARP_COOP or PERSISTENT (AUTO = PERSISTENT); warps_per_cta, ctas_per_sm and
  * chunk (replications per ticket) shape PERSISTENT (0 = default: 32 warps,
  * one CTA per SM, chunks of 16; when no replications are left, a warp
  * finishes its last walkers with all 32 lanes on one walker at a time). */
-mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t n_reps,
+mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                uint64_t seed, int64_t max_steps, int mapping,
                                int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk,
                                int64_t *d_tau, void *stream);
@@ -308,39 +333,45 @@ mrip_status mrip_walk_simulate(const double *radii, int32_t n_dp, int64_t n_reps
  * The call allocates nothing: its scratch (work-stealing ticket, step-cap
  * flag, radius and design-point tables) is a fixed array of 8,448 bytes
  * inside the library, present on every GPU that loads it until the process
- * exits.  Limit: n_dp <= 1024 (larger values return MRIP_EINVAL).  The first
- * call on a device looks the array's address up (cudaGetSymbolAddress) and
- * should therefore come before any stream capture on that device.  Every
- * call reuses the same array -- it resets the ticket and flag itself -- so
- * two calls whose work overlaps on the GPU (different streams, or another
- * thread) race and must not be issued concurrently.  The call waits for its
- * table upload on `stream` before launching.  A replication that reaches
- * max_steps is written as -1; mrip_check_device_flags does not see it. */
-mrip_status mrip_walk_simulate_noalloc(const double *radii, int32_t n_dp, int64_t n_reps,
-                                       uint64_t seed, int64_t max_steps, int mapping,
-                                       int32_t warps_per_cta, int32_t ctas_per_sm,
+ * exits.  Limit: n_dp <= 1024 (larger values return MRIP_EINVAL).  Each call
+ * looks the current device's address of the array up
+ * (cudaGetSymbolAddress), then enqueues a small set-up kernel that writes
+ * the tables (passed as its argument) and clears the ticket and the flag,
+ * then the walk; it copies nothing from host memory and does not wait for
+ * the GPU.  The first lookup on a device can load the library's device
+ * code, so make the first call on each device before any stream capture on
+ * that device.
+ * Every call reuses the same array, so two calls whose work overlaps on the
+ * GPU (different streams, or another thread) race and must not be issued
+ * concurrently; calls on one stream run one after the other.  A replication
+ * that reaches max_steps is written as -1; mrip_check_device_flags does
+ * not see it (scan d_tau for -1). */
+mrip_status mrip_walk_simulate_noalloc(const double *radii, int32_t n_dp, int64_t rep0,
+                                       int64_t n_reps, uint64_t seed, int64_t max_steps,
+                                       int mapping, int32_t warps_per_cta, int32_t ctas_per_sm,
                                        int32_t chunk, int64_t *d_tau, void *stream);
 
 /* Area walk: the paper's random-walk model (Section 5.1, third model) and
  * its WLP-versus-TLP experiment (Section 5.3).  A walker on a 60 x 50
  * periodic map split into 30 areas of 10 x 10 cells (area x/10 + 6 (y/10))
  * starts at (30, 25); move m reads field m mod 64 of block (0, m div 64) of
- * replication `rep`, design point 0 (0:+x 1:-x 2:+y 3:-y); after every move
+ * replication rep0 + r (output column r), design point 0 (0:+x 1:-x 2:+y 3:-y); after every move
  * its area's visit count grows by one.  d_final_area: device int32 n_reps;
  * d_visits: device int32 30 planes of n_reps (may be NULL).  mapping: THREAD
  * (one replication per thread), WARP_1LANE (one per warp, lane 0 -- the
  * paper's WLP) or WARP_COOP (one per warp, lanes share 512-move rounds);
  * AUTO = THREAD.  n_steps <= 2^30. */
-mrip_status mrip_area_walk_simulate(int64_t n_reps, int32_t n_steps, uint64_t seed, int mapping,
-                                    int32_t *d_final_area, int32_t *d_visits, void *stream);
+mrip_status mrip_area_walk_simulate(int64_t rep0, int64_t n_reps, int32_t n_steps, uint64_t seed,
+                                    int mapping, int32_t *d_final_area, int32_t *d_visits,
+                                    void *stream);
 
 /* Monte Carlo pi (paper, Section 5.1, first model).  Draw k of replication
- * `rep` (design point 0) uses words 2(k mod 2), 2(k mod 2)+1 of block
+ * rep0 + r (output r; design point 0) uses words 2(k mod 2), 2(k mod 2)+1 of block
  * (0, k div 2) as integers x, y in [0, 2^32); it hits iff x^2 + y^2 < 2^64.
  * d_hits: device int64 n_reps (cleared, then filled with the hit counts;
  * pi ~ 4 hits / n_draws).  n_draws <= 2^33. */
-mrip_status mrip_pi_simulate(int64_t n_reps, int64_t n_draws, uint64_t seed, int64_t *d_hits,
-                             void *stream);
+mrip_status mrip_pi_simulate(int64_t rep0, int64_t n_reps, int64_t n_draws, uint64_t seed,
+                             int64_t *d_hits, void *stream);
 
 /* Synchronous.  MRIP_ESTEPCAP if any walk launched since the last check hit
  * its step cap (and clears the flag), else MRIP_OK. */

@@ -79,9 +79,9 @@ def mrip_expo(lo, hi, rate, u_out, e_out, stream=None):
 
 
 def mrip_mm1_simulate(dps, n_reps, n_clients, seed, mapping, wait, idle=None, system=None,
-                      stream=None):
+                      stream=None, rep0=0):
     t = _t()
-    _check(lib().mrip_mm1_simulate(_dev(dps, t.float64, "dps"), dps.shape[0], int(n_reps),
+    _check(lib().mrip_mm1_simulate(_dev(dps, t.float64, "dps"), dps.shape[0], int(rep0), int(n_reps),
                                    int(n_clients), int(seed), int(mapping),
                                    _dev(wait, t.float64, allow_none=True),
                                    _dev(idle, t.float64, allow_none=True),
@@ -98,57 +98,58 @@ def mrip_tandem3_simulate(dps, rep0, n_reps, n_clients, window, seed, tag, mappi
 
 
 def mrip_forest_fire_simulate(dps, n_reps, L, n_steps, density, seed, init=None, counts=None,
-                              scalar=None, final=None, stream=None):
+                              scalar=None, final=None, stream=None, rep0=0):
     t = _t()
     _check(lib().mrip_forest_fire_simulate(
-        _dev(dps, t.float64, "dps"), dps.shape[0], int(n_reps), int(L), int(n_steps),
+        _dev(dps, t.float64, "dps"), dps.shape[0], int(rep0), int(n_reps), int(L), int(n_steps),
         float(density), int(seed), _dev(init, t.uint8, allow_none=True),
         _dev(counts, t.int32, allow_none=True), _dev(scalar, t.float64, allow_none=True),
         _dev(final, t.uint8, allow_none=True), _stream(stream)))
 
 
 def mrip_forest_fire_skip_simulate(dps, n_reps, L, n_steps, density, seed, init=None, counts=None,
-                                   scalar=None, final=None, stream=None):
+                                   scalar=None, final=None, stream=None, rep0=0):
     t = _t()
     _check(lib().mrip_forest_fire_skip_simulate(
-        _dev(dps, t.float64, "dps"), dps.shape[0], int(n_reps), int(L), int(n_steps),
+        _dev(dps, t.float64, "dps"), dps.shape[0], int(rep0), int(n_reps), int(L), int(n_steps),
         float(density), int(seed), _dev(init, t.uint8, allow_none=True),
         _dev(counts, t.int32, allow_none=True), _dev(scalar, t.float64, allow_none=True),
         _dev(final, t.uint8, allow_none=True), _stream(stream)))
 
 
 def mrip_walk_simulate(radii, n_reps, seed, max_steps, mapping, tau, warps_per_cta=0,
-                       ctas_per_sm=0, chunk=0, stream=None):
+                       ctas_per_sm=0, chunk=0, stream=None, rep0=0):
     t = _t()
     r, rp = _host(radii, np.float64)
-    _check(lib().mrip_walk_simulate(rp, r.size, int(n_reps), int(seed), int(max_steps),
+    _check(lib().mrip_walk_simulate(rp, r.size, int(rep0), int(n_reps), int(seed), int(max_steps),
                                     int(mapping), int(warps_per_cta), int(ctas_per_sm),
                                     int(chunk), _dev(tau, t.int64, "tau"), _stream(stream)))
 
 
 def mrip_walk_simulate_noalloc(radii, n_reps, seed, max_steps, mapping, tau, warps_per_cta=0,
-                               ctas_per_sm=0, chunk=0, stream=None):
+                               ctas_per_sm=0, chunk=0, stream=None, rep0=0):
     """mrip_walk_simulate for callers that cannot allocate device memory: its
     scratch is a fixed array inside the library (at most 1024 radii); calls
     must not overlap on the GPU."""
     t = _t()
     r, rp = _host(radii, np.float64)
-    _check(lib().mrip_walk_simulate_noalloc(rp, r.size, int(n_reps), int(seed), int(max_steps),
+    _check(lib().mrip_walk_simulate_noalloc(rp, r.size, int(rep0), int(n_reps), int(seed), int(max_steps),
                                             int(mapping), int(warps_per_cta), int(ctas_per_sm),
                                             int(chunk), _dev(tau, t.int64, "tau"),
                                             _stream(stream)))
 
 
-def mrip_area_walk_simulate(n_reps, n_steps, seed, mapping, final_area, visits=None, stream=None):
+def mrip_area_walk_simulate(n_reps, n_steps, seed, mapping, final_area, visits=None, stream=None,
+                            rep0=0):
     t = _t()
-    _check(lib().mrip_area_walk_simulate(int(n_reps), int(n_steps), int(seed), int(mapping),
+    _check(lib().mrip_area_walk_simulate(int(rep0), int(n_reps), int(n_steps), int(seed), int(mapping),
                                          _dev(final_area, t.int32, "final_area"),
                                          _dev(visits, t.int32, allow_none=True), _stream(stream)))
 
 
-def mrip_pi_simulate(n_reps, n_draws, seed, hits, stream=None):
+def mrip_pi_simulate(n_reps, n_draws, seed, hits, stream=None, rep0=0):
     t = _t()
-    _check(lib().mrip_pi_simulate(int(n_reps), int(n_draws), int(seed), _dev(hits, t.int64, "hits"),
+    _check(lib().mrip_pi_simulate(int(rep0), int(n_reps), int(n_draws), int(seed), _dev(hits, t.int64, "hits"),
                                   _stream(stream)))
 
 
@@ -275,6 +276,18 @@ def mrip_run(model, design_points, n_reps, seed):
     _check(lib().mrip_run(model, p, n_dp, int(n_reps), int(seed)))
 
 
+def mrip_run_range(model, design_points, rep_lo, rep_hi, seed):
+    a, p = _host(design_points, np.float64)
+    n_dp = a.shape[0] if a.ndim > 1 else a.size
+    _check(lib().mrip_run_range(model, p, n_dp, int(rep_lo), int(rep_hi), int(seed)))
+
+
+def mrip_moments(model, n_dp):
+    out = np.empty((n_dp, 3))
+    _check(lib().mrip_moments(model, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
 def mrip_run_device(model, d_design_points, n_reps, seed):
     t = _t()
     _check(lib().mrip_run_device(model, _dev(d_design_points, t.float64), d_design_points.shape[0],
@@ -362,6 +375,14 @@ class Model:
         dp = np.asarray(design_points, dtype=np.float64)
         self.n_dp = dp.shape[0] if dp.ndim > 1 else dp.size
         mrip_run(self.h, dp, n_reps, seed)
+
+    def run_range(self, design_points, rep_lo, rep_hi, seed):
+        dp = np.asarray(design_points, dtype=np.float64)
+        self.n_dp = dp.shape[0] if dp.ndim > 1 else dp.size
+        mrip_run_range(self.h, dp, rep_lo, rep_hi, seed)
+
+    def moments(self):
+        return mrip_moments(self.h, self.n_dp)
 
     def run_device(self, d_design_points, n_reps, seed):
         self.n_dp = d_design_points.shape[0]

@@ -65,6 +65,8 @@ SIGNATURES = {
     "mrip_create_model": (_INT, [_INT, _P, _SZ, _P]),
     "mrip_set_stream": (_INT, [_P, _P]),
     "mrip_run": (_INT, [_P, _P, _I32, _I64, _U64]),
+    "mrip_run_range": (_INT, [_P, _P, _I32, _I64, _I64, _U64]),
+    "mrip_moments": (_INT, [_P, _P]),
     "mrip_run_device": (_INT, [_P, _P, _I32, _I64, _U64]),
     "mrip_stats": (_INT, [_P, _D, _P]),
     "mrip_outputs": (_INT, [_P, _INT, _P, _SZ, _INT]),
@@ -77,18 +79,19 @@ SIGNATURES = {
     "mrip_last_error": (ctypes.c_char_p, []),
     "mrip_philox": (_INT, [_P, _P, _I64, _P, _P]),
     "mrip_expo": (_INT, [_P, _P, _P, _I64, _P, _P, _P]),
-    "mrip_mm1_simulate": (_INT, [_P, _I32, _I64, _I64, _U64, _INT, _P, _P, _P, _P]),
+    "mrip_mm1_simulate": (_INT, [_P, _I32, _I64, _I64, _I64, _U64, _INT, _P, _P, _P, _P]),
     "mrip_tandem3_simulate": (_INT, [_P, _I32, _I64, _I64, _I64, _I64, _U64, _U32, _INT, _P, _P,
                                      _P]),
-    "mrip_forest_fire_simulate": (_INT, [_P, _I32, _I64, _I32, _I32, _D, _U64, _P, _P, _P, _P,
-                                         _P]),
-    "mrip_forest_fire_skip_simulate": (_INT, [_P, _I32, _I64, _I32, _I32, _D, _U64, _P, _P, _P,
-                                              _P, _P]),
-    "mrip_walk_simulate": (_INT, [_P, _I32, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P, _P]),
-    "mrip_walk_simulate_noalloc": (_INT, [_P, _I32, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P,
-                                          _P]),
-    "mrip_area_walk_simulate": (_INT, [_I64, _I32, _U64, _INT, _P, _P, _P]),
-    "mrip_pi_simulate": (_INT, [_I64, _I64, _U64, _P, _P]),
+    "mrip_forest_fire_simulate": (_INT, [_P, _I32, _I64, _I64, _I32, _I32, _D, _U64, _P, _P, _P,
+                                         _P, _P]),
+    "mrip_forest_fire_skip_simulate": (_INT, [_P, _I32, _I64, _I64, _I32, _I32, _D, _U64, _P, _P,
+                                              _P, _P, _P]),
+    "mrip_walk_simulate": (_INT, [_P, _I32, _I64, _I64, _U64, _I64, _INT, _I32, _I32, _I32, _P,
+                                  _P]),
+    "mrip_walk_simulate_noalloc": (_INT, [_P, _I32, _I64, _I64, _U64, _I64, _INT, _I32, _I32, _I32,
+                                          _P, _P]),
+    "mrip_area_walk_simulate": (_INT, [_I64, _I64, _I32, _U64, _INT, _P, _P, _P]),
+    "mrip_pi_simulate": (_INT, [_I64, _I64, _I64, _U64, _P, _P]),
     "mrip_check_device_flags": (_INT, []),
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_reduce_i64": (_INT, [_P, _I32, _I64, _P, _P]),

@@ -54,7 +54,7 @@ __device__ void walk_serial(uint32_t rep, int n_steps, const RoundKeys& rk, uint
 }
 
 template <bool kLane0Only>
-__global__ void __launch_bounds__(kThreads) area_walk_serial_kernel(long long n_reps, int n_steps,
+__global__ void __launch_bounds__(kThreads) area_walk_serial_kernel(long long rep0, long long n_reps, int n_steps,
                                                                     const __grid_constant__ RoundKeys rk,
                                                                     int32_t* __restrict__ final_area,
                                                                     int32_t* __restrict__ visits) {
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) area_walk_serial_kernel(long long n_
     if (item >= n_reps) return;
     for (int a = 0; a < kAreas; ++a) hist[a * stride + slot] = 0u;
     int32_t fa;
-    walk_serial(static_cast<uint32_t>(item), n_steps, rk, hist + slot, stride, &fa);
+    walk_serial(static_cast<uint32_t>(rep0 + item), n_steps, rk, hist + slot, stride, &fa);
     final_area[item] = fa;
     if (visits)
         for (int a = 0; a < kAreas; ++a) visits[a * n_reps + item] = static_cast<int32_t>(hist[a * stride + slot]);
@@ -82,7 +82,7 @@ __device__ __forceinline__ int wrap(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-__global__ void __launch_bounds__(kThreads) area_walk_coop_kernel(long long n_reps, int n_steps,
+__global__ void __launch_bounds__(kThreads) area_walk_coop_kernel(long long rep0, long long n_reps, int n_steps,
                                                                   const __grid_constant__ RoundKeys rk,
                                                                   int32_t* __restrict__ final_area,
                                                                   int32_t* __restrict__ visits) {
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) area_walk_coop_kernel(long long n_re
     if (item >= n_reps) return;  // warp-uniform
     if (lane < kAreas) hist[warp][lane] = 0u;
     __syncwarp();
-    const uint32_t rep = static_cast<uint32_t>(item);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item);
     const uint32_t c3 = stream_word(0u, 0u);
     int px = kW / 2, py = kH / 2;  // warp-uniform position before the round
     for (int m0 = 0; m0 < n_steps; m0 += 512) {
@@ -137,23 +137,25 @@ __global__ void __launch_bounds__(kThreads) area_walk_coop_kernel(long long n_re
 
 using namespace mrip;
 
-extern "C" mrip_status mrip_area_walk_simulate(int64_t n_reps, int32_t n_steps, uint64_t seed, int mapping,
-                                               int32_t* d_final_area, int32_t* d_visits, void* stream) {
-    if (n_reps < 0 || n_steps < 0) return fail(MRIP_EINVAL, "mrip_area_walk_simulate: negative size");
-    if (n_reps > 0xFFFFFFFFll) return fail(MRIP_EINVAL, "mrip_area_walk_simulate: n_reps < 2^32");
+extern "C" mrip_status mrip_area_walk_simulate(int64_t rep0, int64_t n_reps, int32_t n_steps, uint64_t seed,
+                                               int mapping, int32_t* d_final_area, int32_t* d_visits,
+                                               void* stream) {
+    if (rep0 < 0 || n_reps < 0 || n_steps < 0) return fail(MRIP_EINVAL, "mrip_area_walk_simulate: negative size");
+    if (rep0 + n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_area_walk_simulate: replication indices < 2^32");
     if (n_steps > (1 << 30)) return fail(MRIP_EINVAL, "mrip_area_walk_simulate: n_steps <= 2^30");
     if (n_reps == 0) return MRIP_OK;
     if (!d_final_area) return fail(MRIP_EINVAL, "mrip_area_walk_simulate: null output");
     const RoundKeys rk = expand_key(seed);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
-        area_walk_serial_kernel<false><<<ceil_div_u(n_reps, kThreads), kThreads, 0, st>>>(n_reps, n_steps, rk,
+        area_walk_serial_kernel<false><<<ceil_div_u(n_reps, kThreads), kThreads, 0, st>>>(rep0, n_reps, n_steps, rk,
                                                                                           d_final_area, d_visits);
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         area_walk_serial_kernel<true><<<ceil_div_u(n_reps * 32, kThreads), kThreads, 0, st>>>(
-            n_reps, n_steps, rk, d_final_area, d_visits);
+            rep0, n_reps, n_steps, rk, d_final_area, d_visits);
     } else if (mapping == MRIP_MAP_WARP_COOP) {
-        area_walk_coop_kernel<<<ceil_div_u(n_reps * 32, kThreads), kThreads, 0, st>>>(n_reps, n_steps, rk,
+        area_walk_coop_kernel<<<ceil_div_u(n_reps * 32, kThreads), kThreads, 0, st>>>(rep0, n_reps, n_steps, rk,
                                                                                      d_final_area, d_visits);
     } else {
         return fail(MRIP_EINVAL, "mrip_area_walk_simulate: mapping must be THREAD, WARP_1LANE or WARP_COOP");

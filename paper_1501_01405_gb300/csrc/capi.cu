@@ -72,13 +72,13 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
     switch (m->kind) {
         case MRIP_MM1: {
             double* w = m->out0.as<double>();
-            s = mrip_mm1_simulate(d_dps, n_dp, n_reps, m->mm1.n_clients, seed, m->plan.mapping, w,
+            s = mrip_mm1_simulate(d_dps, n_dp, m->rep0, n_reps, m->mm1.n_clients, seed, m->plan.mapping, w,
                                   w + items, w + 2 * items, st);
             if (s == MRIP_OK) s = stats_reduce_double(w, n_dp, n_reps, m->nmm2.as<double>(), st, m->spart.as<double>());
             break;
         }
         case MRIP_TANDEM3: {
-            s = mrip_tandem3_simulate(d_dps, n_dp, 0, n_reps, m->tandem.n_clients, m->tandem.window,
+            s = mrip_tandem3_simulate(d_dps, n_dp, m->rep0, n_reps, m->tandem.n_clients, m->tandem.window,
                                       seed, 0, m->plan.mapping, m->out0.as<double>(),
                                       m->out1.as<double>(), st);
             if (s == MRIP_OK)
@@ -86,7 +86,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
             break;
         }
         case MRIP_FOREST_FIRE: {
-            s = mrip_forest_fire_simulate(d_dps, n_dp, n_reps, m->ff.L, m->ff.n_steps, m->ff.density,
+            s = mrip_forest_fire_simulate(d_dps, n_dp, m->rep0, n_reps, m->ff.L, m->ff.n_steps, m->ff.density,
                                           seed, nullptr, m->out0.as<int32_t>(), m->out1.as<double>(),
                                           nullptr, st);
             if (s == MRIP_OK)
@@ -95,7 +95,7 @@ mrip_status enqueue_run(mrip_model* m, uint64_t seed) {
         }
         case MRIP_WALK_L1_EXIT: {
             const int32_t* tab = m->walk_tab.as<int32_t>();
-            s = walk_launch(tab, tab + n_dp, n_dp, n_reps, seed, m->walk.max_steps, m->plan.mapping,
+            s = walk_launch(tab, tab + n_dp, n_dp, m->rep0, n_reps, seed, m->walk.max_steps, m->plan.mapping,
                             m->plan.warps_per_cta, m->plan.ctas_per_sm, m->plan.chunk,
                             m->out0.as<int64_t>(), m->ticket.as<unsigned long long>(), st);
             if (s == MRIP_OK)
@@ -153,8 +153,8 @@ mrip_status run_common(mrip_model* m, int32_t n_dp, int64_t n_reps, uint64_t see
         if (e != cudaSuccess) return cuda_status(e, "mrip_run: table upload");
         if (!device_error_flags()) return fail(MRIP_ENOMEM, "device error flags");
     }
-    const bool reuse = m->exec && m->g_n_dp == n_dp && m->g_n_reps == n_reps && m->g_seed == seed &&
-                       same_plan(m->g_plan, m->plan);
+    const bool reuse = m->exec && m->g_n_dp == n_dp && m->g_n_reps == n_reps && m->g_rep0 == m->rep0 &&
+                       m->g_seed == seed && same_plan(m->g_plan, m->plan);
     if (!reuse) {
         if (m->exec) {
             cudaGraphExecDestroy(m->exec);
@@ -198,6 +198,7 @@ mrip_status run_common(mrip_model* m, int32_t n_dp, int64_t n_reps, uint64_t see
         }
         m->g_n_dp = n_dp;
         m->g_n_reps = n_reps;
+        m->g_rep0 = m->rep0;
         m->g_seed = seed;
         m->g_plan = m->plan;
     }
@@ -207,9 +208,11 @@ mrip_status run_common(mrip_model* m, int32_t n_dp, int64_t n_reps, uint64_t see
     return MRIP_OK;
 }
 
-mrip_status check_shape(mrip_model* m, int32_t n_dp, int64_t n_reps) {
+mrip_status check_shape(mrip_model* m, int32_t n_dp, int64_t n_reps, int64_t rep0 = 0) {
     if (n_dp < 1 || n_dp >= (1 << 24)) return fail(MRIP_EINVAL, "mrip_run: n_dp in 1..2^24-1");
     if (n_reps < 1 || n_reps > 0xFFFFFFFFll) return fail(MRIP_EINVAL, "mrip_run: n_reps in 1..2^32-1");
+    if (rep0 < 0 || rep0 + n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_run_range: 0 <= rep_lo < rep_hi <= 2^32");
     if (m->kind == MRIP_FOREST_FIRE && static_cast<long long>(n_dp) * n_reps > 0x7FFFFFFFll)
         return fail(MRIP_EINVAL, "mrip_run: forest fire needs n_dp * n_reps < 2^31");
     return MRIP_OK;
@@ -416,11 +419,13 @@ extern "C" mrip_status mrip_set_stream(mrip_model* m, void* cuda_stream) {
     return MRIP_OK;
 }
 
-extern "C" mrip_status mrip_run(mrip_model* m, const double* design_points, int32_t n_dp, int64_t n_reps,
-                                uint64_t seed) {
+extern "C" mrip_status mrip_run_range(mrip_model* m, const double* design_points, int32_t n_dp, int64_t rep_lo,
+                                      int64_t rep_hi, uint64_t seed) {
     if (!m || !design_points) return fail(MRIP_EINVAL, "mrip_run: null argument");
-    mrip_status s = check_shape(m, n_dp, n_reps);
+    const int64_t n_reps = rep_hi - rep_lo;
+    mrip_status s = check_shape(m, n_dp, n_reps, rep_lo);
     if (s != MRIP_OK) return s;
+    m->rep0 = rep_lo;
     s = check_dps(m->kind, design_points, n_dp);
     if (s != MRIP_OK) return s;
     const size_t nval = static_cast<size_t>(n_dp) * dp_dim(m->kind);
@@ -433,11 +438,17 @@ extern "C" mrip_status mrip_run(mrip_model* m, const double* design_points, int3
     return run_common(m, n_dp, n_reps, seed);
 }
 
+extern "C" mrip_status mrip_run(mrip_model* m, const double* design_points, int32_t n_dp, int64_t n_reps,
+                                uint64_t seed) {
+    return mrip_run_range(m, design_points, n_dp, 0, n_reps, seed);
+}
+
 extern "C" mrip_status mrip_run_device(mrip_model* m, const double* d_design_points, int32_t n_dp,
                                        int64_t n_reps, uint64_t seed) {
     if (!m || !d_design_points) return fail(MRIP_EINVAL, "mrip_run_device: null argument");
     mrip_status s = check_shape(m, n_dp, n_reps);
     if (s != MRIP_OK) return s;
+    m->rep0 = 0;
     const size_t nval = static_cast<size_t>(n_dp) * dp_dim(m->kind);
     s = prepare(m, n_dp, n_reps);
     if (s != MRIP_OK) return s;
@@ -466,6 +477,17 @@ extern "C" mrip_status mrip_stats(mrip_model* m, double conf, mrip_stat* out) {
     if (e != cudaSuccess) return cuda_status(e, "mrip_stats");
     mrip_status s = mrip_stats_finalize(h.data(), m->n_dp, conf, out);
     if (s != MRIP_OK) return s;
+    if (m->kind == MRIP_WALK_L1_EXIT) return mrip_check_device_flags();
+    return MRIP_OK;
+}
+
+extern "C" mrip_status mrip_moments(mrip_model* m, double* nmm2_out) {
+    if (!m || !nmm2_out) return fail(MRIP_EINVAL, "mrip_moments: null argument");
+    if (!m->has_run) return fail(MRIP_ESTATE, "mrip_moments: no run yet");
+    cudaError_t e = cudaMemcpyAsync(nmm2_out, m->nmm2.p, static_cast<size_t>(m->n_dp) * 3 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_status(e, "mrip_moments");
     if (m->kind == MRIP_WALK_L1_EXIT) return mrip_check_device_flags();
     return MRIP_OK;
 }

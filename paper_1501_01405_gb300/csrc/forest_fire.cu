@@ -617,18 +617,18 @@ mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, 
 }
 }  // namespace mrip
 
-extern "C" mrip_status mrip_forest_fire_skip_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+extern "C" mrip_status mrip_forest_fire_skip_simulate(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                                       int32_t L, int32_t n_steps, double density,
                                                       uint64_t seed, const uint8_t* d_init,
                                                       int32_t* d_counts, double* d_scalar,
                                                       uint8_t* d_final, void* stream) {
-    if (n_dp < 0 || n_reps < 0 || n_steps < 0)
+    if (n_dp < 0 || n_reps < 0 || n_steps < 0 || rep0 < 0)
         return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: negative size");
     if (L < 32 || L > 512 || L % 32 != 0 || (L & (L - 1)) != 0)
         return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: L must be 32, 64, 128, 256 or 512");
     if (!(density >= 0.0 && density < 1.0))
         return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: density must be in [0, 1)");
-    if (n_dp >= (1 << 24) || n_reps > 0x100000000ll)
+    if (n_dp >= (1 << 24) || rep0 + n_reps > 0x100000000ll)
         return fail(MRIP_EINVAL, "mrip_forest_fire_skip_simulate: n_dp < 2^24 and replication indices < 2^32");
     const long long n_items = static_cast<long long>(n_dp) * n_reps;
     if (n_items == 0) return MRIP_OK;
@@ -644,21 +644,21 @@ extern "C" mrip_status mrip_forest_fire_skip_simulate(const double* d_dps, int32
     const uint32_t t_dens = threshold32(density);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (L) {
-        case 32: rc = launch_ff_skip<1>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
-        case 64: rc = launch_ff_skip<2>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
-        case 128: rc = launch_ff_skip<4>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
-        case 256: rc = launch_ff_skip<8>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
-        case 512: rc = launch_ff_skip<16>(d_dps, n_items, n_reps, 0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 32: rc = launch_ff_skip<1>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 64: rc = launch_ff_skip<2>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 128: rc = launch_ff_skip<4>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 256: rc = launch_ff_skip<8>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
+        case 512: rc = launch_ff_skip<16>(d_dps, n_items, n_reps, rep0, n_steps, t_dens, rk, tab, d_init, d_counts, d_scalar, d_final, st); break;
     }
     if (rc != MRIP_OK) return rc;
     return launch_status("mrip_forest_fire_skip_simulate");
 }
 
-extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                                  int32_t L, int32_t n_steps, double density,
                                                  uint64_t seed, const uint8_t* d_init,
                                                  int32_t* d_counts, double* d_scalar,
                                                  uint8_t* d_final, void* stream) {
-    return forest_fire_launch(d_dps, n_dp, 0, n_reps, L, n_steps, density, seed, d_init, d_counts,
+    return forest_fire_launch(d_dps, n_dp, rep0, n_reps, L, n_steps, density, seed, d_init, d_counts,
                               d_scalar, d_final, static_cast<cudaStream_t>(stream));
 }

@@ -54,11 +54,13 @@ struct mrip_model {
     std::vector<double> host_dps;
     int32_t n_dp = 0;
     int64_t n_reps = 0;
+    int64_t rep0 = 0;  // replication index of output column 0 (mrip_run_range)
     bool has_run = false;
     // graph cache
     cudaGraphExec_t exec = nullptr;
     int32_t g_n_dp = -1;
     int64_t g_n_reps = -1;
+    int64_t g_rep0 = -1;
     uint64_t g_seed = 0;
     Plan g_plan;
     ~mrip_model() {
@@ -70,7 +72,7 @@ namespace mrip {
 int dp_dim(int kind);
 mrip_status check_dps(int kind, const double* dps, int32_t n_dp);
 mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_pos, int32_t n_dp,
-                        int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
+                        int64_t rep0, int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
                         int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
                         unsigned long long* d_ticket, cudaStream_t st);
 mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>& r_by_pos,

@@ -23,7 +23,7 @@ __device__ __forceinline__ uint32_t inside(uint32_t x, uint32_t y) {
     return x2 <= ~y2 ? 1u : 0u;
 }
 
-__global__ void __launch_bounds__(kPiThreads) pi_kernel(long long n_draws, long long chunks,
+__global__ void __launch_bounds__(kPiThreads) pi_kernel(long long n_draws, long long chunks, long long rep0,
                                                         const __grid_constant__ RoundKeys rk,
                                                         unsigned long long* __restrict__ hits) {
     __shared__ uint32_t part[kPiThreads / 32];
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kPiThreads) pi_kernel(long long n_draws, long 
     const uint32_t c3 = stream_word(0u, 0u);
     uint32_t cnt = 0;
     for (long long b = start / 2 + threadIdx.x; 2 * b < end; b += kPiThreads) {
-        const uint4 w = philox(0u, static_cast<uint32_t>(b), static_cast<uint32_t>(rep), c3, rk);
+        const uint4 w = philox(0u, static_cast<uint32_t>(b), static_cast<uint32_t>(rep0 + rep), c3, rk);
         cnt += inside(w.x, w.y);
         if (2 * b + 1 < end) cnt += inside(w.z, w.w);
     }
@@ -52,11 +52,11 @@ __global__ void __launch_bounds__(kPiThreads) pi_kernel(long long n_draws, long 
 
 using namespace mrip;
 
-extern "C" mrip_status mrip_pi_simulate(int64_t n_reps, int64_t n_draws, uint64_t seed, int64_t* d_hits,
-                                        void* stream) {
-    if (n_reps < 0 || n_draws < 0) return fail(MRIP_EINVAL, "mrip_pi_simulate: negative size");
-    if (n_reps > 0xFFFFFFFFll || n_draws > (1LL << 33))
-        return fail(MRIP_EINVAL, "mrip_pi_simulate: n_reps < 2^32, n_draws <= 2^33");
+extern "C" mrip_status mrip_pi_simulate(int64_t rep0, int64_t n_reps, int64_t n_draws, uint64_t seed,
+                                        int64_t* d_hits, void* stream) {
+    if (rep0 < 0 || n_reps < 0 || n_draws < 0) return fail(MRIP_EINVAL, "mrip_pi_simulate: negative size");
+    if (rep0 + n_reps > 0x100000000ll || n_draws > (1LL << 33))
+        return fail(MRIP_EINVAL, "mrip_pi_simulate: replication indices < 2^32, n_draws <= 2^33");
     if (n_reps == 0) return MRIP_OK;
     if (!d_hits) return fail(MRIP_EINVAL, "mrip_pi_simulate: null output");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -66,6 +66,6 @@ extern "C" mrip_status mrip_pi_simulate(int64_t n_reps, int64_t n_draws, uint64_
     const long long chunks = (n_draws + kPiChunk - 1) / kPiChunk;
     if (chunks * n_reps > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_pi_simulate: too many draws in total");
     pi_kernel<<<static_cast<unsigned>(chunks * n_reps), kPiThreads, 0, st>>>(
-        n_draws, chunks, expand_key(seed), reinterpret_cast<unsigned long long*>(d_hits));
+        n_draws, chunks, rep0, expand_key(seed), reinterpret_cast<unsigned long long*>(d_hits));
     return launch_status("mrip_pi_simulate");
 }

@@ -106,7 +106,7 @@ __device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp
 
 template <bool kLane0Only>
 __global__ void __launch_bounds__(128, 8) mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
-                                  long long n_reps, long long n_clients,
+                                  long long n_reps, long long rep0, long long n_clients,
                                   const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     long long item;
     if (kLane0Only) {
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(128, 8) mm1_serial_kernel(const double* __rest
     }
     if (item >= n_items) return;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
-    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
     const double inv = static_cast<double>(n_clients);
     if (fix_rate_ok(lam) && fix_rate_ok(mu)) {  // 48-bit fixed-point times
@@ -181,7 +181,7 @@ __device__ __forceinline__ MaxPlus compose(MaxPlus f, MaxPlus g) {
 // One warp per replication; clients staged in shared memory when kStage.
 template <bool kStage>
 __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n_items,
-                                     long long n_reps, long long n_clients,
+                                     long long n_reps, long long rep0, long long n_clients,
                                      const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     extern __shared__ double stage[];  // per warp: S[seg_cap*32], A[seg_cap*32]
     const int lane = threadIdx.x & 31;
@@ -189,7 +189,7 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
     const long long item = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5;
     if (item >= n_items) return;  // warp-uniform
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
-    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const double inv_lam = 0x1p-57 / dps[2 * dp], inv_mu = 0x1p-57 / dps[2 * dp + 1];
     const long long seg = (n_clients + 31) / 32;
     const long long lo = lane * seg;
@@ -777,7 +777,7 @@ struct Mm1Sums128 {
 
 
 __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict__ dps, long long n_reps,
-                                                       long long n_clients, bool staged,
+                                                       long long rep0, long long n_clients, bool staged,
                                                        const __grid_constant__ RoundKeys rk, LogTable tab,
                                                        Mm1Out out) {
     extern __shared__ long long fix_stage[];  // [client - lo][thread] x (S, A) when staged
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const long long item = blockIdx.x;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
-    const uint32_t rep = static_cast<uint32_t>(item % n_reps);
+    const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const double lam = dps[2 * dp], mu = dps[2 * dp + 1];
     const uint32_t c3 = stream_word(0u, dp);
     const long long k = (n_clients + blockDim.x - 1) / blockDim.x;
@@ -1048,14 +1048,14 @@ __global__ void __launch_bounds__(1024) tandem3_cta_kernel(const double* __restr
 
 using namespace mrip;
 
-extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int64_t n_reps,
+extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                          int64_t n_clients, uint64_t seed, int mapping,
                                          double* d_wait, double* d_idle, double* d_system,
                                          void* stream) {
-    if (n_dp < 0 || n_reps < 0 || n_clients < 1)
-        return fail(MRIP_EINVAL, "mrip_mm1_simulate: need n_dp >= 0, n_reps >= 0, n_clients >= 1");
-    if (n_dp >= (1 << 24) || n_reps > 0xFFFFFFFFll || n_clients > 0xFFFFFFFFll)
-        return fail(MRIP_EINVAL, "mrip_mm1_simulate: n_dp < 2^24, n_reps and n_clients <= 2^32-1");
+    if (n_dp < 0 || n_reps < 0 || rep0 < 0 || n_clients < 1)
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: need n_dp, n_reps, rep0 >= 0 and n_clients >= 1");
+    if (n_dp >= (1 << 24) || rep0 + n_reps > 0x100000000ll || n_clients > 0xFFFFFFFFll)
+        return fail(MRIP_EINVAL, "mrip_mm1_simulate: n_dp < 2^24, replication indices < 2^32, n_clients <= 2^32-1");
     const long long n_items = static_cast<long long>(n_dp) * n_reps;
     if (n_items == 0) return MRIP_OK;
     if (!d_dps) return fail(MRIP_EINVAL, "mrip_mm1_simulate: null design points");
@@ -1067,10 +1067,10 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_THREAD) {
         mm1_serial_kernel<false><<<ceil_div_u(n_items, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, n_clients, rk, tab, out);
+            d_dps, n_items, n_reps, rep0, n_clients, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_1LANE) {
         mm1_serial_kernel<true><<<ceil_div_u(n_items * 32, 128), 128, 0, st>>>(
-            d_dps, n_items, n_reps, n_clients, rk, tab, out);
+            d_dps, n_items, n_reps, rep0, n_clients, rk, tab, out);
     } else if (mapping == MRIP_MAP_CTA) {
         if (n_items > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_mm1_simulate: too many replications for CTA");
         // about 4 clients per thread, 32 .. 1024 threads; fixed-point variates
@@ -1086,7 +1086,7 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
             if (e != cudaSuccess) return cuda_status(e, "mrip_mm1_simulate: shared memory attribute");
         }
         mm1_cta_kernel<<<static_cast<unsigned>(n_items), static_cast<unsigned>(threads), staged ? stage : 0, st>>>(
-            d_dps, n_reps, n_clients, staged, rk, tab, out);
+            d_dps, n_reps, rep0, n_clients, staged, rk, tab, out);
     } else if (mapping == MRIP_MAP_WARP_COOP) {
         const long long seg = (n_clients + 31) / 32;
         const size_t per_warp = static_cast<size_t>(seg) * 32 * 2 * sizeof(double);
@@ -1098,10 +1098,10 @@ extern "C" mrip_status mrip_mm1_simulate(const double* d_dps, int32_t n_dp, int6
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem));
             mm1_warp_coop_kernel<true><<<ceil_div_u(n_items, warps), 32 * warps, smem, st>>>(
-                d_dps, n_items, n_reps, n_clients, rk, tab, out);
+                d_dps, n_items, n_reps, rep0, n_clients, rk, tab, out);
         } else {
             mm1_warp_coop_kernel<false><<<ceil_div_u(n_items, 4), 128, 0, st>>>(
-                d_dps, n_items, n_reps, n_clients, rk, tab, out);
+                d_dps, n_items, n_reps, rep0, n_clients, rk, tab, out);
         }
     } else {
         return fail(MRIP_EINVAL, "mrip_mm1_simulate: mapping must be THREAD, WARP_1LANE, WARP_COOP or CTA");

@@ -28,7 +28,6 @@
 //               16-move words, a warp scan of their displacements gives each
 //               lane's start, and a ballot finds the first exit.
 #include <algorithm>
-#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -45,6 +44,7 @@ struct WalkJob {
     const int32_t* radius;  // by processing position k
     const int32_t* dp_of;   // design point by processing position k
     long long n_reps;
+    long long rep0;         // replication index of output column 0
     long long total;
     long long max_steps;
     long long chunk;
@@ -268,10 +268,11 @@ __device__ __forceinline__ void decode(const WalkJob& job, long long g, int& R, 
         k = static_cast<long long>(__umul64hi(static_cast<unsigned long long>(g), job.reps_magic));
         if (g - k * job.n_reps < 0) --k;
     }
-    rep = static_cast<uint32_t>(g - k * job.n_reps);
+    const long long r = g - k * job.n_reps;
+    rep = static_cast<uint32_t>(job.rep0 + r);
     R = job.radius[k];
     dp = static_cast<uint32_t>(job.dp_of[k]);
-    out = static_cast<long long>(dp) * job.n_reps + rep;
+    out = static_cast<long long>(dp) * job.n_reps + r;
 }
 
 // Whole replication on one thread (THREAD and WARP_1LANE mappings).
@@ -452,13 +453,14 @@ unsigned long long reps_reciprocal(long long n) {
 
 // Launch on device-resident (radius, dp) tables in processing order.
 mrip_status walk_launch(const int32_t* d_radius_by_pos, const int32_t* d_dp_by_pos, int32_t n_dp,
-                        int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
+                        int64_t rep0, int64_t n_reps, uint64_t seed, int64_t max_steps, int mapping,
                         int32_t warps_per_cta, int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
                         unsigned long long* d_ticket, cudaStream_t st) {
     WalkJob job;
     job.radius = d_radius_by_pos;
     job.dp_of = d_dp_by_pos;
     job.n_reps = n_reps;
+    job.rep0 = rep0;
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
     job.chunk = chunk > 0 ? chunk : 16;
@@ -517,8 +519,11 @@ mrip_status walk_tables(const double* radii, int32_t n_dp, std::vector<int32_t>&
 // Its scratch (work-stealing ticket, step-cap flag, radius and design-point
 // tables) lives in one file-scope device array instead of library-allocated
 // buffers.  Host code cannot pass the array's name to a kernel (in host code
-// it is only a stand-in); each device's address is looked up once with
-// cudaGetSymbolAddress while that device is current.
+// it is only a stand-in): every call looks the current device's address up
+// with cudaGetSymbolAddress.  The tables travel to the GPU as a kernel
+// argument (at most 8 KiB), and a one-CTA set-up kernel writes them and
+// clears the ticket and the flag, so the call neither copies from host
+// memory nor waits for the GPU.
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxDp = 1024;
 constexpr size_t kNoAllocHeader = 256;  // [0, 8) ticket, [8, 12) step-cap flag
@@ -527,25 +532,24 @@ constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * sizeof(int32_t) * kNoAlloc
 static __device__ __align__(256) unsigned char g_walk_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[64] = {nullptr};
+struct NoAllocTables {
+    int32_t r_by_pos[kNoAllocMaxDp];
+    int32_t dp_by_pos[kNoAllocMaxDp];
+    int32_t n_dp;
+};
 
-mrip_status noalloc_scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= 64) return fail(MRIP_EUNSUPPORTED, "mrip_walk_simulate_noalloc: device index >= 64");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_walk_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
-                               "mrip_walk_simulate_noalloc: cudaGetSymbolAddress");
-        g_noalloc_addr[dev] = ptr;
+__global__ void __launch_bounds__(256) walk_noalloc_setup(const __grid_constant__ NoAllocTables t,
+                                                          unsigned char* base) {
+    int32_t* d_r = reinterpret_cast<int32_t*>(base + kNoAllocHeader);
+    int32_t* d_d = d_r + t.n_dp;
+    for (int i = threadIdx.x; i < t.n_dp; i += blockDim.x) {
+        d_r[i] = t.r_by_pos[i];
+        d_d[i] = t.dp_by_pos[i];
     }
-    *out = g_noalloc_addr[dev];
-    return MRIP_OK;
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<unsigned long long*>(base) = 0ull;  // ticket
+        *reinterpret_cast<int*>(base + 8) = 0;                 // step-cap flag
+    }
 }
 }  // namespace
 
@@ -553,37 +557,40 @@ mrip_status noalloc_scratch_address(void** out) {
 
 using namespace mrip;
 
-extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n_dp, int64_t n_reps,
-                                                  uint64_t seed, int64_t max_steps, int mapping,
-                                                  int32_t warps_per_cta, int32_t ctas_per_sm,
-                                                  int32_t chunk, int64_t* d_tau, void* stream) {
-    if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: negative size");
+extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n_dp, int64_t rep0,
+                                                  int64_t n_reps, uint64_t seed, int64_t max_steps,
+                                                  int mapping, int32_t warps_per_cta,
+                                                  int32_t ctas_per_sm, int32_t chunk, int64_t* d_tau,
+                                                  void* stream) {
+    if (n_dp < 0 || n_reps < 0 || rep0 < 0)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: negative size");
     if (n_dp > kNoAllocMaxDp)
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: n_dp " + std::to_string(n_dp) +
                                      " exceeds its fixed scratch limit of " +
                                      std::to_string(kNoAllocMaxDp) + " design points");
-    if (n_reps > 0xFFFFFFFFll) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: n_reps < 2^32");
+    if (rep0 + n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: replication indices < 2^32");
     if (max_steps < 1 || max_steps > (1LL << 38))
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: max_steps in 1..2^38");
     if (chunk < 0 || chunk > (1 << 20))
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: chunk in 0..2^20");
     if (static_cast<long long>(n_dp) * n_reps == 0) return MRIP_OK;
     if (!radii || !d_tau) return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: null pointer");
-    // processing order on the stack: largest radius first (stable insertion sort)
-    int32_t r_by_pos[kNoAllocMaxDp];
-    int32_t dp_by_pos[kNoAllocMaxDp];
+    // processing order: largest radius first (stable insertion sort)
+    NoAllocTables t;
+    t.n_dp = n_dp;
     for (int32_t i = 0; i < n_dp; ++i) {
         const double r = radii[i];
         if (!(r >= 1.0 && r <= 65536.0) || r != static_cast<double>(static_cast<int32_t>(r)))
             return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: R must be an integer in 1..65536");
         int32_t pos = i;
-        while (pos > 0 && r_by_pos[pos - 1] < static_cast<int32_t>(r)) {
-            r_by_pos[pos] = r_by_pos[pos - 1];
-            dp_by_pos[pos] = dp_by_pos[pos - 1];
+        while (pos > 0 && t.r_by_pos[pos - 1] < static_cast<int32_t>(r)) {
+            t.r_by_pos[pos] = t.r_by_pos[pos - 1];
+            t.dp_by_pos[pos] = t.dp_by_pos[pos - 1];
             --pos;
         }
-        r_by_pos[pos] = static_cast<int32_t>(r);
-        dp_by_pos[pos] = i;
+        t.r_by_pos[pos] = static_cast<int32_t>(r);
+        t.dp_by_pos[pos] = i;
     }
     if (mapping != MRIP_MAP_AUTO && mapping != MRIP_MAP_PERSISTENT && mapping != MRIP_MAP_THREAD &&
         mapping != MRIP_MAP_WARP_1LANE && mapping != MRIP_MAP_WARP_COOP)
@@ -593,25 +600,28 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     if (wpc > 32 || cps > 64)
         return fail(MRIP_EINVAL, "mrip_walk_simulate_noalloc: warps_per_cta <= 32, ctas_per_sm <= 64");
 
+    // this device's address of the array (looked up on every call: cheap, and
+    // never stale)
     void* base_v = nullptr;
-    mrip_status s = noalloc_scratch_address(&base_v);
-    if (s != MRIP_OK) return s;
+    cudaError_t e = cudaGetSymbolAddress(&base_v, g_walk_noalloc_scratch);
+    if (e != cudaSuccess || !base_v)
+        return cuda_status(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                           "mrip_walk_simulate_noalloc: cudaGetSymbolAddress");
     unsigned char* base = static_cast<unsigned char*>(base_v);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms < 1) return cuda_status(e, "mrip_walk_simulate_noalloc: SM count");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t tab = static_cast<size_t>(n_dp) * sizeof(int32_t);
-    int32_t* d_r = reinterpret_cast<int32_t*>(base + kNoAllocHeader);
-    int32_t* d_d = reinterpret_cast<int32_t*>(base + kNoAllocHeader + tab);
-    // the ticket and the flag must start at zero; the tables are overwritten
-    cudaError_t e = cudaMemsetAsync(base, 0, 16, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_r, r_by_pos, tab, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_d, dp_by_pos, tab, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables live on this stack frame
-    if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate_noalloc: scratch set-up");
+    walk_noalloc_setup<<<1, 256, 0, st>>>(t, base);
+    mrip_status s = launch_status("mrip_walk_simulate_noalloc: set-up");
+    if (s != MRIP_OK) return s;
 
     WalkJob job;
-    job.radius = d_r;
-    job.dp_of = d_d;
+    job.radius = reinterpret_cast<int32_t*>(base + kNoAllocHeader);
+    job.dp_of = job.radius + n_dp;
     job.n_reps = n_reps;
+    job.rep0 = rep0;
     job.total = static_cast<long long>(n_dp) * n_reps;
     job.max_steps = max_steps;
     job.chunk = chunk > 0 ? chunk : 16;
@@ -620,10 +630,6 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     job.ticket = reinterpret_cast<unsigned long long*>(base);
     job.err = reinterpret_cast<int*>(base + 8);
     const RoundKeys rk = expand_key(seed);
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess || sms < 1) return cuda_status(e, "mrip_walk_simulate_noalloc: SM count");
     if (mapping == MRIP_MAP_AUTO || mapping == MRIP_MAP_PERSISTENT) {
         walk_persistent_kernel<<<sms * cps, 32 * wpc, 0, st>>>(job, rk);
     } else if (mapping == MRIP_MAP_THREAD) {
@@ -636,13 +642,13 @@ extern "C" mrip_status mrip_walk_simulate_noalloc(const double* radii, int32_t n
     return launch_status("mrip_walk_simulate_noalloc");
 }
 
-extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int64_t n_reps,
+extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int64_t rep0, int64_t n_reps,
                                           uint64_t seed, int64_t max_steps, int mapping,
                                           int32_t warps_per_cta, int32_t ctas_per_sm,
                                           int32_t chunk, int64_t* d_tau, void* stream) {
-    if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_walk_simulate: negative size");
-    if (n_dp >= (1 << 24) || n_reps > 0xFFFFFFFFll)
-        return fail(MRIP_EINVAL, "mrip_walk_simulate: n_dp < 2^24 and n_reps < 2^32");
+    if (n_dp < 0 || n_reps < 0 || rep0 < 0) return fail(MRIP_EINVAL, "mrip_walk_simulate: negative size");
+    if (n_dp >= (1 << 24) || rep0 + n_reps > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_walk_simulate: n_dp < 2^24 and replication indices < 2^32");
     if (max_steps < 1 || max_steps > (1LL << 38))
         return fail(MRIP_EINVAL, "mrip_walk_simulate: max_steps in 1..2^38");
     if (chunk < 0 || chunk > (1 << 20)) return fail(MRIP_EINVAL, "mrip_walk_simulate: chunk in 0..2^20");
@@ -662,6 +668,6 @@ extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_d, dp_by_pos.data(), tab, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors die at return
     if (e != cudaSuccess) return cuda_status(e, "mrip_walk_simulate: table upload");
-    return walk_launch(d_r, d_d, n_dp, n_reps, seed, max_steps, mapping, warps_per_cta, ctas_per_sm,
+    return walk_launch(d_r, d_d, n_dp, rep0, n_reps, seed, max_steps, mapping, warps_per_cta, ctas_per_sm,
                        chunk, d_tau, reinterpret_cast<unsigned long long*>(base), st);
 }

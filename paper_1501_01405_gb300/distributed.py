@@ -6,7 +6,8 @@ so ranks need no collective on the data path.  Two layouts are supported:
 * independent batches (weak scaling): rank r runs the whole workload with
   seed + r; the only cross-rank operation is the max of the timed seconds;
 * shards of one experiment: rank r runs the contiguous replication range
-  shard_range(n_reps, r, world); its per-design-point (n, mean, M2) triples
+  shard_range(n_reps, r, world) through mrip_run_range (run_shard,
+  sharded_stats); its per-design-point (n, mean, M2) triples
   are all-gathered (n_dp x 24 bytes per rank) and merged in rank order by
   mrip_stats_merge, which gives the same interval on every rank.
 
@@ -46,6 +47,33 @@ def gather_merge_stats(nmm2, device=None):
     dist.all_gather(parts, t)
     stacked = np.stack([p.cpu().numpy() for p in parts])
     return mrip_stats_merge(stacked)
+
+
+def run_shard(model, design_points, n_reps, seed, rank, world):
+    """Run this rank's replication range of one experiment through the engine
+    (mrip_run_range) and return its per-design-point (n, mean, M2) triples."""
+    lo, hi = shard_range(n_reps, rank, world)
+    if hi <= lo:  # more ranks than replications: an empty part
+        n_dp = np.asarray(design_points).shape[0]
+        return np.zeros((n_dp, 3))
+    model.run_range(design_points, lo, hi, seed)
+    return model.moments()
+
+
+def sharded_stats(model, design_points, n_reps, seed, conf=0.95, device=None):
+    """Intervals of one experiment whose replications are split across the
+    ranks of the process group: each rank runs its shard, the triples are
+    all-gathered and merged in rank order, and every rank gets the same
+    intervals (those of one run of all n_reps replications, up to the
+    rounding of the merge)."""
+    from . import mrip_stats_finalize
+    rank, world = 0, 1
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        rank, world = dist.get_rank(), dist.get_world_size()
+    local = run_shard(model, design_points, n_reps, seed, rank, world)
+    merged = gather_merge_stats(local, device)
+    return mrip_stats_finalize(merged, conf), merged
 
 
 def collect_with_recovery(store, rank, world, local_nmm2, recompute, timeout_s=5.0):

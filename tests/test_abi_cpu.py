@@ -99,12 +99,27 @@ def test_invalid_arguments_rejected_on_host():
         eng.mrip_t_crit(1.5, 3)
     L = eng.lib()
     # stage entry points validate sizes before touching the device
-    assert L.mrip_mm1_simulate(None, -1, 1, 1, 0, 0, None, None, None, None) == 1
-    assert L.mrip_forest_fire_simulate(None, 1, 1, 100, 10, 0.5, 0, None, None, None, None,
+    assert L.mrip_mm1_simulate(None, -1, 0, 1, 1, 0, 0, None, None, None, None) == 1
+    assert L.mrip_forest_fire_simulate(None, 1, 0, 1, 100, 10, 0.5, 0, None, None, None, None,
                                        None) == 1
     r = (ctypes.c_double * 1)(2.5)
-    assert L.mrip_walk_simulate(r, 1, 4, 0, 100, 0, 0, 0, 0, ctypes.c_void_p(16), None) == 1
+    assert L.mrip_walk_simulate(r, 1, 0, 4, 0, 100, 0, 0, 0, 0, ctypes.c_void_p(16), None) == 1
     assert b"integer" in L.mrip_last_error()
+    # replication ranges: indices must stay below 2^32, rep0 >= 0
+    assert L.mrip_mm1_simulate(None, 1, (1 << 32) - 1, 2, 10, 0, 0, None, None, None, None) == 1
+    assert b"2^32" in L.mrip_last_error()
+    assert L.mrip_pi_simulate(-1, 1, 10, 0, None, None) == 1
+    assert L.mrip_area_walk_simulate(1 << 32, 1, 10, 0, 0, None, None, None) == 1
+    assert L.mrip_forest_fire_skip_simulate(None, 1, -3, 1, 32, 10, 0.5, 0, None, None, None,
+                                            None, None) == 1
+    assert L.mrip_walk_simulate_noalloc(r, 1, 1 << 32, 4, 0, 100, 0, 0, 0, 0,
+                                        ctypes.c_void_p(16), None) == 1
+    m = eng.Model(eng.MRIP_MM1, n_clients=10)
+    for lo, hi in ((5, 5), (7, 3), (-1, 4), (0, (1 << 32) + 1)):
+        with pytest.raises(eng.MripError) as e:
+            m.run_range([[0.5, 1.0]], lo, hi, 42)
+        assert e.value.code == 1
+    m.close()
 
 
 def test_plan_json_round_trip_and_rejection():
