@@ -7,9 +7,13 @@
 A step is one pass of the hot path over one batch of synthetic input: all
 replications of the workload simulated by the CUDA kernels and reduced to
 per-design-point (n, mean, M2) on the device.  The default workload is the
-128x128 forest fire (1,024 replications x 1,000 steps); the others are
+largest configuration, the 256x256 forest fire with 64 design points
+(ff256: 128 replications each x 2,000 steps); the line also carries the
+replications/s of the other configurations (mm1_32, ff128, walk8, tandem;
+"configs") and the plain-vs-control-variate time to the target half-width
+on the tandem and ff256 workloads ("time_to_target").  Other workloads are
 selectable: mm1_32 (latency; its step replays as one CUDA graph), mm1_64k
-(throughput), walk8, tandem, ff256, ff128_skip / ff256_skip (skip-sampled
+(throughput), walk8, tandem, ff128, ff128_skip / ff256_skip (skip-sampled
 lattice events), area_walk and pi (the paper's own models; --sweep times
 them against the replication count).
 
@@ -19,9 +23,11 @@ value   = replications / s over the K timed steps, inputs resident in HBM,
 e2e     = the same through the public model-handle API (mrip_run with host
           design points + mrip_stats reading the intervals back), wall time.
 roofline= the dominant kernel's algorithmic work per launch / its mean event
-          time, against the nominal integer-multiply rate (SMs x multiplies
-          per clock x maximum SM clock): every model is bound by Philox's
-          32x32->64 products, not by HBM or the tensor cores.
+          time.  Lattices: integer instructions per cell-update against the
+          issue rate (SMs x 4 warp instructions per clock x maximum SM clock),
+          with the integer-multiply unit beside it ("alt"); the other models
+          against the nominal integer-multiply rate: every model is bound by
+          Philox's 32x32->64 products, not by HBM or the tensor cores.
 cpu_baseline = the oracle (plain C) on a bounded sample of the same workload
           on all host cores (rank 0, N = 1 only).
 
@@ -69,6 +75,19 @@ MULS_PER_FIXED_VARIATE = 34
 PROFILED_TRAFFIC = {"forest_fire_kernel<4>": 36864}
 
 
+# Issue slots: 4 schedulers per SM, one warp instruction each per clock.
+ISSUE_PER_CLK_SM = 4
+# Integer instructions per forest-fire cell-update: a quarter of a
+# Philox4x32-10 block (15-20 integer instructions) plus the bit-parallel
+# rule (32 cells per word); the midpoint 17.5 is the algorithmic figure.
+FF_INSTR_PER_CELL = 17.5
+
+
+def issue_peak_g():
+    """Warp instructions per second (G) at the maximum SM clock."""
+    return SMS * ISSUE_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
+
+
 def imul_peak_gops():
     return SMS * IMUL_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e9
 
@@ -80,12 +99,27 @@ class Workload:
     name = ""
     units_name = "replications"
     dtype = ""
+    rep0 = 0  # first replication of this rank's shard (sharded mode)
 
     def __init__(self, rank):
         self.rank = rank
 
     def config(self):
         raise NotImplementedError
+
+    def shard(self, rank, world):
+        """Run only this rank's replication range of the one experiment
+        (same seed on every rank); returns the experiment's replication
+        count over all design points."""
+        from paper_1501_01405_gb300.distributed import shard_range
+        full = self.units()
+        lo, hi = shard_range(self.w["n_reps"], rank, world)
+        if hi <= lo:
+            raise SystemExit("--shard: more ranks than replications")
+        self.w["n_reps"] = hi - lo
+        self.rep0 = lo
+        self.seed = self.w["seed"]
+        return full
 
 
 class ForestFire(Workload):
@@ -125,7 +159,7 @@ class ForestFire(Workload):
             k_start.record()
         self.eng.mrip_forest_fire_simulate(self.d_dps, w["n_reps"], w["L"], w["n_steps"],
                                            w["density"], self.seed, None, self.counts,
-                                           self.scalar)
+                                           self.scalar, rep0=self.rep0)
         if k_end is not None:
             k_end.record()
         self.eng.mrip_stats_reduce(self.scalar.view(w["n_dp"], w["n_reps"]), self.nmm2)
@@ -135,12 +169,19 @@ class ForestFire(Workload):
     def roofline_work(self):
         w = self.w
         cells = w["L"] * w["L"] * w["n_steps"] * self.units()
+        alt = dict(unit="Gop/s (32-bit integer multiply)",
+                   work=cells * INT_MULS_PER_PHILOX / 4.0, peak=imul_peak_gops(),
+                   peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
+                       SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
+                   per_unit="10 int multiplies per cell-update (1/4 Philox block)")
         return dict(kernel="forest_fire_kernel<%d>" % (w["L"] // 32), bound="alu",
-                    unit="Gop/s (32-bit integer multiply)",
-                    work=cells * INT_MULS_PER_PHILOX / 4.0, peak=imul_peak_gops(),
-                    peak_source="nominal: %d SMs x %d int-mul/clk x %.0f MHz" % (
-                        SMS, IMUL_PER_CLK_SM, SM_MAX_MHZ),
-                    per_unit="10 int multiplies per cell-update (1/4 Philox block)")
+                    unit="G warp-instructions/s",
+                    work=cells * FF_INSTR_PER_CELL / 32.0, peak=issue_peak_g(),
+                    peak_source="issue slots: %d SMs x %d warp-instr/clk x %.0f MHz" % (
+                        SMS, ISSUE_PER_CLK_SM, SM_MAX_MHZ),
+                    per_unit="%.1f integer instructions per cell-update (1/4 Philox4x32-10 "
+                             "block + the bit-parallel rule), 32 per warp instruction"
+                             % FF_INSTR_PER_CELL, alt=alt)
 
     def extra_rates(self, reps_per_s, torch):
         w = self.w
@@ -186,7 +227,7 @@ class ForestFireSkip(ForestFire):
             k_start.record()
         self.eng.mrip_forest_fire_skip_simulate(self.d_dps, w["n_reps"], w["L"], w["n_steps"],
                                                 w["density"], self.seed, None, self.counts,
-                                                self.scalar)
+                                                self.scalar, rep0=self.rep0)
         if k_end is not None:
             k_end.record()
         self.eng.mrip_stats_reduce(self.scalar.view(w["n_dp"], w["n_reps"]), self.nmm2)
@@ -249,7 +290,7 @@ class Walk(Workload):
         if k_start is not None:
             k_start.record()
         self.eng.mrip_walk_simulate(self.radii, self.w["n_reps"], self.seed, 1 << 38,
-                                    self.eng.MRIP_MAP_PERSISTENT, self.tau)
+                                    self.eng.MRIP_MAP_PERSISTENT, self.tau, rep0=self.rep0)
         if k_end is not None:
             k_end.record()
         self.eng.mrip_stats_reduce_i64(self.tau.view(len(self.radii), self.w["n_reps"]), self.nmm2)
@@ -340,9 +381,9 @@ class Queue(Workload):
         if self.key in ("mm1_32", "mm1_64k"):
             mapping = self.eng.MRIP_MAP_CTA if self.key == "mm1_32" else self.eng.MRIP_MAP_THREAD
             self.eng.mrip_mm1_simulate(self.d_dps, w["n_reps"], w["n_clients"], self.seed,
-                                       mapping, self.y)
+                                       mapping, self.y, rep0=self.rep0)
         else:
-            self.eng.mrip_tandem3_simulate(self.d_dps, 0, w["n_reps"], w["n_clients"],
+            self.eng.mrip_tandem3_simulate(self.d_dps, self.rep0, w["n_reps"], w["n_clients"],
                                            w["window"], self.seed, 0, self.eng.MRIP_MAP_THREAD,
                                            self.y, self.feat)
         if k_end is not None:
@@ -655,32 +696,39 @@ def make_workload(name, rank):
 # ---------------------------------------------------------------------------
 # time to a target interval half-width, plain vs learned control variate
 # ---------------------------------------------------------------------------
-CV_DEFAULTS = dict(train_frac=0.1, epochs=20, batch=1024, lr=1e-3)
+CV_DEFAULTS = dict(train_frac=0.1, val_frac=0.1, epochs=20, patience=3, batch=1024, lr=1e-3,
+                   gate=True, m_ctrl=0)
+PHASES = ("ms_simulate", "ms_train", "ms_control", "ms_infer", "ms_estimate")
 
 
 def _median_hw(stats):
     return float(np.median([s["half_width"] for s in stats]))
 
 
-def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10, which="tandem_cv"):
-    """Tandem workload (4,096 design points x 10,000 clients) or the 256x256
-    forest fire (64 design points x 2,000 steps): the target is the median
-    plain 95 % half-width at n_reps replications.  The plain estimator
-    reaches it by definition in the time of that run; the control-variate
-    estimator is run at n_reps, its replication count is scaled by
-    (half-width ratio)^2 to the target, and it is run again at that count,
-    timed end to end (simulation, training, control runs, inference,
-    estimator)."""
+def time_to_target(eng, torch, stream, seed, which="tandem_cv"):
+    """Tandem workload (4,096 design points x 10,000 clients, 256
+    replications) or the 256x256 forest fire (64 design points x 2,000 steps,
+    128 replications): the target is the median plain 95 % half-width at
+    n_reps replications, which the plain estimator reaches by definition in
+    the time of that run.  The control-variate estimator (mrip_run_cv:
+    network on 10 % of the replications with a 10 % validation split and
+    early stopping, control runs sized from the validation rho^2, the gate
+    on) is run at n_reps; if it declines, its result is the plain interval
+    and its time that of the whole call; otherwise its replication count is
+    scaled by (half-width ratio)^2 and it is run again at that count.  Every
+    run is timed end to end (wall clock around the synchronous call) and
+    carries the library's CUDA-event breakdown of its phases."""
     w = mrip_inputs.workload(which)
+    n_reps = w["n_reps"]
     if which == "tandem_cv":
         model = eng.Model(eng.MRIP_TANDEM3, n_clients=w["n_clients"], window=w["window"])
-        label = ("tandem_cv: 3-station tandem, 4096 design points, 10000 clients, network 8-64-64-1 "
-                 "on 10 percent of replications, {} control runs per held-out replication").format(m_factor)
+        label = ("tandem_cv: 3-station tandem, 4096 design points, 10000 clients, %d replications, "
+                 "network 8-64-64-1 on 10 percent of replications" % n_reps)
     else:
         model = eng.Model(eng.MRIP_FOREST_FIRE, L=w["L"], n_steps=w["n_steps"], density=w["density"],
                           window=w["window"])
-        label = ("ff256_cv: forest fire 256x256, 64 design points, 2000 steps, network 6-64-64-1 on "
-                 "10 percent of replications, {} control runs per held-out replication").format(m_factor)
+        label = ("ff256_cv: forest fire 256x256, 64 design points, 2000 steps, %d replications, "
+                 "network 6-64-64-1 on 10 percent of replications" % n_reps)
     model.set_stream(stream)
 
     def timed(fn):
@@ -691,8 +739,16 @@ def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10, which="tan
         return out, time.perf_counter() - t0
 
     def cv_run(n):
-        n_train = math.ceil(CV_DEFAULTS["train_frac"] * n)
-        return model.run_cv(w["dps"], n, seed, m_ctrl=m_factor * (n - n_train), **CV_DEFAULTS)
+        return model.run_cv(w["dps"], n, seed, **CV_DEFAULTS)
+
+    def summary(n, secs, cv, rep):
+        d = {"replications": n, "seconds": secs, "median_half_width": _median_hw(cv),
+             "declined": rep["declined"], "val_rho2": rep["val_rho2"],
+             "var_ratio_predicted": rep["var_ratio"], "control_runs_per_dp": rep["m_ctrl"],
+             "epochs_run": rep["epochs_run"], "best_epoch": rep["best_epoch"],
+             "train_loss": rep["train_loss"], "val_loss": rep["val_loss"]}
+        d["phases_ms"] = {k[3:]: rep[k] for k in PHASES}
+        return d
 
     model.run(w["dps"], n_reps, seed)  # warm (graph capture, allocations)
     model.stats()
@@ -700,28 +756,79 @@ def time_to_target(eng, torch, stream, seed, n_reps=256, m_factor=10, which="tan
     plain = model.stats()
     target = _median_hw(plain)
     cv_run(n_reps)  # warm
-    (pl, cv, loss), t_cv0 = timed(lambda: cv_run(n_reps))
-    hw0 = _median_hw(cv)
-    n_held0 = cv[0]["n"]
-    n_need = max(n_reps // 8, int(math.ceil(n_held0 * (hw0 / target) ** 2
-                                             / (1 - CV_DEFAULTS["train_frac"]))))
-    (pl2, cv2, loss2), t_cv = timed(lambda: cv_run(n_need))
-    # held-out plain half-width at equal replications (what the network buys)
-    y = model.outputs(0 if which == "tandem_cv" else 1).reshape(w["n_dp"], n_need)  # per-replication Y
-    n_tr = math.ceil(CV_DEFAULTS["train_frac"] * n_need)
-    ratio = [c["half_width"] / (np.std(y[d, n_tr:], ddof=1) / math.sqrt(n_need - n_tr)
-                                * c["t_crit"]) for d, c in enumerate(cv2)]
+    (pl, cv, rep), t_cv0 = timed(lambda: cv_run(n_reps))
+    at_n = summary(n_reps, t_cv0, cv, rep)
+    if rep["declined"]:
+        final, t_cv, n_need = at_n, t_cv0, n_reps
+    else:
+        hw0 = _median_hw(cv)
+        n_held0 = cv[0]["n"]
+        n_need = max(n_reps // 8, int(math.ceil(n_held0 * (hw0 / target) ** 2
+                                                 / (1 - CV_DEFAULTS["train_frac"]))))
+        (pl2, cv2, rep2), t_cv = timed(lambda: cv_run(n_need))
+        final = summary(n_need, t_cv, cv2, rep2)
+    # the break-even rho^2: with this run's overhead (everything but the
+    # plain simulation), M sized for a tenth of the residual variance and
+    # 10 % of the replications spent on training, the control variate reaches
+    # the plain half-width in the plain time when (1 - rho^2) 1.1 / 0.9 =
+    # 1 - overhead / simulation
+    ph = at_n["phases_ms"]
+    t_sim = ph["simulate"]
+    over = sum(v for k, v in ph.items() if k != "simulate")
+    rho2_be = 1.0 - (1.0 - over / t_sim) * (1 - CV_DEFAULTS["train_frac"]) / 1.1 if t_sim > 0 else None
     model.close()
     return {"workload": label,
             "target_half_width": target,
-            "plain": {"replications": n_reps, "seconds": t_plain,
-                      "median_half_width": target},
-            "cv_at_same_replications": {"replications": n_reps, "seconds": t_cv0,
-                                        "median_half_width": hw0, "train_loss": loss},
-            "cv": {"replications": n_need, "seconds": t_cv,
-                   "median_half_width": _median_hw(cv2), "train_loss": loss2},
+            "plain": {"replications": n_reps, "seconds": t_plain, "median_half_width": target},
+            "cv_at_same_replications": at_n,
+            "cv": final,
             "cv_over_plain_time": t_cv / t_plain,
-            "median_cv_over_plain_half_width_same_heldout": float(np.median(ratio))}
+            "break_even_val_rho2": rho2_be,
+            "note": "declined: the gate returned the plain interval (the plain estimator is the "
+                    "fallback), so the time above is the plain run plus training and validation"
+            if final["declined"] else "accepted: control runs and inference included"}
+
+
+def config_rates(eng, torch, steps=5, warmup=3):
+    """replications/s of the other configurations (device time, CUDA events,
+    L2 flushed between steps): M/M/1 (config 0, one CUDA graph per step), the
+    128^2 forest fire (config 1), the walk batch (config 2) and the plain
+    tandem (config 3)."""
+    out = {}
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    for name in ("mm1_32", "ff128", "walk8", "tandem"):
+        wl = make_workload(name, 0)
+        wl.setup(eng, torch)
+        step = wl.step
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        graph = None
+        if getattr(wl, "graph_step", False):
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                wl.step()
+            torch.cuda.synchronize()
+            step = graph.replay
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+        n = steps if name != "mm1_32" else 50
+        ms = []
+        for i in range(n):
+            flush.fill_(float(i))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = sum(ms) / len(ms)
+        out[name] = {"replications_per_s": wl.units() / (t / 1e3), "ms_per_step": t,
+                     "steps": n, "workload": wl.config()["workload"]}
+        del graph
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -840,20 +947,29 @@ def reference_arm(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def e2e_model(wl, model, stream, torch, steps, barrier, world, total_units):
-    """mrip_run with host design points + mrip_stats reading the intervals back."""
+def e2e_model(wl, model, stream, torch, steps, barrier, world, total_units, sharded=False):
+    """mrip_run with host design points + mrip_stats reading the intervals back;
+    sharded: mrip_run_range over this rank's replications, mrip_moments, and
+    the triples all-gathered and merged (every rank gets the intervals of the
+    whole experiment)."""
     import torch.distributed as dist
+    from paper_1501_01405_gb300.distributed import gather_merge_stats
     model.set_stream(stream)
     dps, n_reps = wl.e2e_inputs()
-    for _ in range(3):
+
+    def one():
+        if sharded:
+            model.run_range(dps, wl.rep0, wl.rep0 + n_reps, wl.seed)
+            return gather_merge_stats(model.moments(), device="cuda")
         model.run(dps, n_reps, wl.seed)
-        model.stats(0.95)
+        return model.stats(0.95)
+    for _ in range(3):
+        one()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        model.run(dps, n_reps, wl.seed)
-        model.stats(0.95)
+        one()
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
@@ -899,9 +1015,9 @@ def e2e_stage(wl, torch, steps, barrier, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="ff128",
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="ff256",
                     choices=["ff128", "ff256", "ff128_skip", "ff256_skip", "walk8", "mm1_32", "mm1_64k", "tandem",
                              "area_walk", "pi"])
     ap.add_argument("--sweep", action="store_true",
@@ -918,6 +1034,11 @@ def main():
                     help="--impl reference: host seconds for the whole run (each step 0.2 .. 8 s)")
     ap.add_argument("--no-cv", action="store_true",
                     help="skip the plain-vs-control-variate time-to-target measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the replications/s of the other configurations")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split the replications of one experiment across the "
+                         "ranks (strong scaling) instead of one batch per rank")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -928,6 +1049,7 @@ def main():
     wl = make_workload(args.workload, rank)
     if args.n_dp > 0:
         shrink(wl, args.n_dp)
+    full_units = wl.shard(rank, world) if args.shard else None
 
     if args.impl == "reference":
         reference_arm(args, wl, rank, world)
@@ -1004,7 +1126,7 @@ def main():
         tt = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dev_ms = float(tt.item())
-    total_units = wl.units() * args.steps * world
+    total_units = (full_units if args.shard else wl.units() * world) * args.steps
     value = total_units / (dev_ms / 1e3)
 
     # ---- end to end through the public API, host buffers
@@ -1012,7 +1134,8 @@ def main():
     if model is None:  # stage entry point: launch, then read the outputs back
         e2e = e2e_stage(wl, torch, args.steps, barrier, world)
     else:
-        e2e = e2e_model(wl, model, stream, torch, args.steps, barrier, world, total_units)
+        e2e = e2e_model(wl, model, stream, torch, args.steps, barrier, world, total_units,
+                        sharded=args.shard)
     if model is None:
         e2e["value"] = total_units / e2e.pop("seconds")
     # ---- roofline of the dominant kernel
@@ -1025,13 +1148,22 @@ def main():
             "traffic": PROFILED_TRAFFIC.get(rw["kernel"]) if args.n_dp == 0 else None,
             "kernel_ms": kmean, "per_unit": rw["per_unit"],
             "peak_source": rw["peak_source"]}
+    if "alt" in rw:
+        alt = rw["alt"]
+        a_ach = alt["work"] / (kmean / 1e3) / 1e9
+        roof["alt"] = {"achieved": a_ach, "peak": alt["peak"], "unit": alt["unit"],
+                       "frac": a_ach / alt["peak"], "per_unit": alt["per_unit"],
+                       "peak_source": alt["peak_source"]}
 
     line = {"metric": METRIC, "value": value, "unit": "replications/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak",
+            "vs_baseline": None,
             "dtype": wl.dtype, "data": "synthetic (seeded Philox streams)",
             "config": dict(wl.config(), l2="flushed between timed steps (256 MiB write)",
-                           parallelism="replicas x%d (independent seeds)" % world),
+                           parallelism=("one experiment, replications split over %d ranks "
+                                        "(mrip_run_range shards, triples merged)" % world)
+                           if args.shard else "replicas x%d (independent seeds)" % world),
             "roofline": roof, "e2e": e2e, "clocks": clk,
             "gpu_launches": wl.launches_per_step * args.steps,
             "wall_s": t_wall}
@@ -1040,11 +1172,11 @@ def main():
     if extra:
         line["rates"] = extra
     if rank == 0 and world == 1 and not args.no_cv:
-        if args.workload in ("ff256", "ff256_skip"):
-            line["time_to_target"] = time_to_target(eng, torch, stream, 42, n_reps=128, m_factor=2,
-                                                    which="ff256_cv")
-        else:
-            line["time_to_target"] = time_to_target(eng, torch, stream, 42)
+        line["time_to_target"] = {
+            "tandem_cv": time_to_target(eng, torch, stream, 42, which="tandem_cv"),
+            "ff256_cv": time_to_target(eng, torch, stream, 42, which="ff256_cv")}
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "ff256":
+        line["configs"] = config_rates(eng, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         threads = oracle.host_threads()

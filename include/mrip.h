@@ -19,8 +19,10 @@
  * SC'11) with key = (seed low 32 bits, seed high 32 bits) and counter
  *   c0 = sub-block index within a step, c1 = step index,
  *   c2 = replication index,             c3 = (tag << 24) | design point,
- * tags 0 simulation, 1 lattice initial state, 2 control-mean runs,
- * 3 network initialisation, 4 minibatch order.  (The paper split one
+ * tags 0 simulation (the control variate's control runs are further
+ * replications of tag 0), 1 lattice initial state, 3 network
+ * initialisation, 4 minibatch order, 5 and 6 the skip-sampled forest fire's
+ * growth and lightning events (2 is unused).  (The paper split one
  * Tausworthe stream by random spacing, Section 5; a counter-based generator
  * lets any replication be recomputed alone.)  Hence design points < 2^24 and
  * replication indices < 2^32.
@@ -198,25 +200,82 @@ mrip_status mrip_autotune(mrip_model *model, const double *design_points, int32_
                           int64_t n_reps, uint64_t seed, int trials, const char *cache_path);
 
 /* Learned control variate (engine extension; the paper's estimator is the
- * plain mean of Section 1).  Runs the replications, trains the network
- * d_in -> 64 -> 64 -> 1 (d_in 8 for TANDEM3, 6 for FOREST_FIRE) on the first
- * ceil(train_frac * n_reps) replications of every design point with the
- * engine's own kernels, predicts the held-out replications and `m_ctrl`
- * control-mean runs per design point (tag 2, early window only), and writes
- * per-design-point plain (all n_reps) and control-variate intervals into the
- * caller's host arrays.  Synchronous. */
+ * plain mean of Section 1, which stays the fallback and the judge).
+ * Synchronous.  Steps:
+ *   1. runs the n_reps replications of every design point and writes the
+ *      plain intervals (all n_reps) into plain_out;
+ *   2. trains the network d_in -> 64 -> 64 -> 1 (d_in 8 for TANDEM3: lambda,
+ *      mu1..3 and the means of the first `window` gaps and services; 6 for
+ *      FOREST_FIRE: log10 p_grow, log10 p_lightning and the mean burning
+ *      fraction of the four quarters of the first `window` steps) with
+ *      mrip_mlp_train on the first n_fit of the n_train = ceil(train_frac
+ *      n_reps) training replications of every design point; the other
+ *      n_val = ceil(val_frac n_train) are the validation set (early stop,
+ *      `patience`).  Inputs and target are standardised with the fit set's
+ *      FP64 mean and population standard deviation;
+ *   3. from the validation replications, estimates rho^2, the pooled
+ *      within-design-point squared correlation of Y and the prediction g
+ *      (each design point's deviations divided by its own standard
+ *      deviations of Y and g over its fit replications, so that every
+ *      design point weighs the same), and sizes the control runs: m_ctrl = 0 asks for
+ *      M = ceil(n_held rho^2 / (0.1 (1 - rho^2))), clamped to
+ *      [2, 100 n_held], so that the control mean adds at most a tenth to
+ *      the residual variance (10 n_held without validation);
+ *   4. gate != 0: predicts the variance ratio of the control-variate and
+ *      plain estimators at this n, n_reps ((1 - rho^2) / n_held + rho^2 / M),
+ *      and when it is >= 1 declines: cv_out gets the plain intervals
+ *      (m = 0, beta = 0) and report->declined = 1;
+ *   5. otherwise predicts g for the n_held = n_reps - n_train held-out
+ *      replications and for the M control runs -- the replications
+ *      n_reps .. n_reps + M - 1 of the same streams (tag 0), simulated for
+ *      the early window only -- and writes per design point
+ *      beta = Cov(Y, g) / Var(g), mean(Y) - beta (mean(g) - mean(g_ctrl)),
+ *      var = s_r^2 / n_held + beta^2 Var(g_ctrl) / M and the Student-t
+ *      interval on n_held - 2 degrees of freedom into cv_out.
+ * report (may be NULL) receives the counts, losses, rho^2 and the CUDA-event
+ * time of each phase. */
 typedef struct {
-    double train_frac;   /* in (0, 1), e.g. 0.1                      */
-    int32_t epochs;      /* >= 1                                      */
-    int32_t batch;       /* >= 1                                      */
+    double train_frac;   /* in (0, 1), e.g. 0.1                                 */
+    double val_frac;     /* in [0, 1): share of the training replications kept  */
+                         /* for validation; 0: no validation, no gate           */
+    int32_t epochs;      /* >= 1 (the maximum when validating)                  */
+    int32_t patience;    /* >= 0: early stop on the validation loss (0: never)  */
+    int32_t batch;       /* >= 1                                                */
+    int32_t gate;        /* != 0: decline the control variate when it cannot    */
+                         /* beat the plain estimator at this n                  */
     float lr, beta1, beta2, eps;
-    int64_t m_ctrl;      /* control-mean runs per design point >= 2    */
-    double conf;         /* interval confidence in (0, 1)             */
-    uint64_t net_seed;   /* network initialisation and minibatch order */
+    int64_t m_ctrl;      /* control runs per design point: 0 = sized as above,  */
+                         /* else >= 2                                           */
+    double conf;         /* interval confidence in (0, 1)                       */
+    uint64_t net_seed;   /* network initialisation and minibatch order          */
 } mrip_cv_params;
+
+typedef struct {
+    int32_t declined;    /* 1: cv_out holds the plain intervals                 */
+    int32_t epochs_run;
+    int32_t best_epoch;  /* the epoch whose parameters were kept (1-based)      */
+    int32_t n_val;       /* validation replications per design point            */
+    int64_t m_ctrl;      /* control runs per design point (0 when declined)     */
+    float train_loss;    /* mean minibatch loss of the last epoch run           */
+    float val_loss;      /* validation loss of the kept epoch (NaN: none)       */
+    double val_rho2;     /* pooled within-design-point rho^2 (NaN: none)        */
+    double var_ratio;    /* predicted Var(control variate) / Var(plain) (NaN)   */
+    double ms_simulate;  /* plain run and intervals                             */
+    double ms_train;     /* features, standardisation, training, validation     */
+    double ms_control;   /* control runs and their features                     */
+    double ms_infer;     /* predictions of held-out and control replications    */
+    double ms_estimate;  /* per-design-point estimator and read-back            */
+} mrip_cv_report;
+
 mrip_status mrip_run_cv(mrip_model *model, const double *design_points, int32_t n_dp,
                         int64_t n_reps, uint64_t seed, const mrip_cv_params *params,
-                        mrip_stat *plain_out, mrip_cv_stat *cv_out, float *train_loss_out);
+                        mrip_stat *plain_out, mrip_cv_stat *cv_out, mrip_cv_report *report);
+
+/* Synchronous.  The network of the handle's last mrip_run_cv: its
+ * parameters (host float[mrip_mlp_param_count(d_in)], may be NULL) and the
+ * standardisation (host double[2 (d_in + 1)]: mean and std of each input,
+ * then of the target; may be NULL).  MRIP_ESTATE before any mrip_run_cv. */
+mrip_status mrip_cv_network(mrip_model *model, float *theta_out, double *norm_out);
 
 void mrip_destroy(mrip_model *model);
 
@@ -426,6 +485,45 @@ mrip_status mrip_mlp_forward(const float *d_theta, int32_t d_in, const float *d_
 mrip_status mrip_mlp_loss_grad(const float *d_theta, int32_t d_in, const float *d_x,
                                const float *d_y, int64_t n, const int64_t *d_idx,
                                int64_t B, float *d_grad, float *d_loss, void *stream);
+
+/* Training of the network on the tensor cores: the kernel mrip_run_cv uses.
+ * One launch on a cluster of 8 CTAs runs every Adam step (Kingma & Ba, with
+ * bias correction, steps counted from 1) of every epoch; the four 64-wide
+ * contractions of a 128-sample tile run as tcgen05 MMAs with BF16 operands
+ * and FP32 accumulators in tensor memory.  Epoch e visits the n samples in
+ * the order pi(i) = (a i + b) mod n from block (0, e) of stream tag 4 under
+ * order_seed (a = 1 + w0 mod (n - 1), stepped up to the first value coprime
+ * with n; b = w1 mod n); minibatch k is positions k B .. min(k B + B, n) - 1,
+ * the loss the mean of (yhat - y)^2 over it.  With a validation set
+ * (n_val > 0), the mean squared error over it is evaluated after every
+ * epoch; the parameters of the epoch with the lowest value are kept, and
+ * training stops after `patience` epochs without a lower value (0: never).
+ * Arguments (device unless stated; "may be NULL" outputs are skipped):
+ *   d_x, d_y      float, d_in planes of n, and n (standardised inputs/target)
+ *   d_xv, d_yv    the validation set, d_in planes of n_val, and n_val
+ *   d_theta       in: initial parameters (mrip_mlp_param_count floats);
+ *                 out: the trained ones (the kept epoch's with validation)
+ *   d_losses      per Adam step (may be NULL; room for every step run)
+ *   d_grad        the gradient of the last step (may be NULL)
+ *   d_m, d_v      Adam's moments after the last step (may be NULL)
+ *   d_val_losses  per epoch (may be NULL)
+ *   info_out      HOST int32[3]: epochs run, epoch kept (1-based), steps run
+ *                 (may be NULL)
+ * Synchronous (it reads back the kernel's status).  An MMA that does not
+ * complete within its wait limit returns MRIP_ECUDA. */
+typedef struct {
+    int64_t batch;        /* minibatch size >= 1                              */
+    int32_t epochs;       /* >= 1                                             */
+    int32_t patience;     /* >= 0; early stop on the validation loss          */
+    int64_t max_steps;    /* > 0: stop after this many Adam steps; 0: none    */
+    float lr, beta1, beta2, eps;
+    uint64_t order_seed;  /* minibatch order (stream tag 4)                   */
+} mrip_train_params;
+mrip_status mrip_mlp_train(int32_t d_in, const float *d_x, const float *d_y, int64_t n,
+                           const float *d_xv, const float *d_yv, int64_t n_val,
+                           const mrip_train_params *params, float *d_theta, float *d_losses,
+                           float *d_grad, float *d_m, float *d_v, float *d_val_losses,
+                           int32_t *info_out, void *stream);
 
 /* One Adam step (Kingma & Ba) with bias correction; step t >= 1. */
 mrip_status mrip_adam_step(float *d_theta, float *d_m, float *d_v, const float *d_grad,

@@ -188,21 +188,31 @@ def adam_step(theta, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def train(X, y, d_in, seed, epochs, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
-          eps=1e-8, master_fp32=True):
+          eps=1e-8, master_fp32=True, X_val=None, y_val=None, patience=0):
     """Full training run in FP64 (masters rounded to FP32 after each step when
-    master_fp32).  Returns (theta, (x_mean, x_std, y_mean, y_std), losses)."""
+    master_fp32).  With a validation set (X_val, y_val; standardised with the
+    training set's moments) the mean squared error over it is taken after
+    every epoch; the parameters of the epoch with the lowest value are kept,
+    and training stops after `patience` epochs without a lower value
+    (0: never).  Returns (theta, (x_mean, x_std, y_mean, y_std), losses,
+    info) with info = {val_losses, epochs_run, best_epoch}."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64).reshape(-1)
     xm, xs = standardizer(X)
     ym, ys = standardizer(y)
     Xs = apply_std(X, xm, xs)
     ysd = apply_std(y[:, None], ym, ys)[:, 0]
+    have_val = X_val is not None and len(X_val) > 0
+    if have_val:
+        Xv = apply_std(np.asarray(X_val, dtype=np.float64), xm, xs)
+        yv = apply_std(np.asarray(y_val, dtype=np.float64).reshape(-1, 1), ym, ys)[:, 0]
     theta = init_params(d_in, seed)
     m = np.zeros_like(theta)
     v = np.zeros_like(theta)
     n = X.shape[0]
     t = 0
-    losses = []
+    losses, val_losses = [], []
+    best, best_theta, best_epoch, bad, epochs_run = math.inf, theta, 0, 0, 0
     for e in range(epochs):
         order = batch_order(n, e, seed)
         for k in range(0, n, batch):
@@ -213,7 +223,23 @@ def train(X, y, d_in, seed, epochs, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
             if master_fp32:
                 theta = f32(theta)
             losses.append(loss)
-    return theta, (xm, xs, ym[0], ys[0]), np.array(losses)
+        epochs_run = e + 1
+        if have_val:
+            yhat, _ = forward(theta, Xv, d_in)
+            vl = math.fsum(((yhat - yv) ** 2).tolist()) / len(yv)
+            val_losses.append(vl)
+            if vl < best:
+                best, best_theta, best_epoch, bad = vl, theta, e + 1, 0
+            else:
+                bad += 1
+                if patience > 0 and bad >= patience:
+                    break
+    if have_val:
+        theta = best_theta
+    else:
+        best_epoch = epochs_run
+    info = dict(val_losses=np.array(val_losses), epochs_run=epochs_run, best_epoch=best_epoch)
+    return theta, (xm, xs, ym[0], ys[0]), np.array(losses), info
 
 
 def predict(theta, X, norm, d_in):

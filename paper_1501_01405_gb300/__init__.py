@@ -14,9 +14,10 @@ import numpy as np
 from ._abi import (MRIP_MAP_AUTO, MRIP_MAP_CTA, MRIP_MAP_PERSISTENT, MRIP_MAP_THREAD,  # noqa: F401
                    MRIP_MAP_WARP_1LANE, MRIP_MAP_WARP_COOP, MRIP_MM1, MRIP_TANDEM3,
                    MRIP_FOREST_FIRE, MRIP_WALK_L1_EXIT, STATUS_NAMES, MripError,
-                   MripLibraryMissing, mrip_cv_params, mrip_cv_stat, mrip_forest_fire_params,
-                   mrip_mm1_params, mrip_stat, mrip_tandem3_params, mrip_walk_params, lib,
-                   library_path)
+                   MripLibraryMissing, mrip_cv_params, mrip_cv_report, mrip_cv_stat,
+                   mrip_forest_fire_params,
+                   mrip_mm1_params, mrip_stat, mrip_tandem3_params, mrip_train_params,
+                   mrip_walk_params, lib, library_path)
 from ._abi import check as _check
 
 __all__ = [n for n in dir() if n.startswith("mrip_") or n.startswith("MRIP_")] + [
@@ -228,6 +229,31 @@ def mrip_adam_step(theta, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps
                                 float(beta1), float(beta2), float(eps), _stream(stream)))
 
 
+def mrip_mlp_train(d_in, x, y, theta, batch, epochs, order_seed, lr=1e-3, beta1=0.9, beta2=0.999,
+                   eps=1e-8, max_steps=0, patience=0, xv=None, yv=None, losses=None, grad=None,
+                   m=None, v=None, val_losses=None, stream=None):
+    """Tensor-core training (synchronous).  x: float (d_in, n) planes; xv, yv
+    the optional validation set.  Returns (epochs run, epoch kept, steps run)."""
+    t = _t()
+    n = x.shape[1]
+    n_val = 0 if xv is None else xv.shape[1]
+    prm = mrip_train_params(batch=int(batch), epochs=int(epochs), patience=int(patience),
+                            max_steps=int(max_steps), lr=lr, beta1=beta1, beta2=beta2, eps=eps,
+                            order_seed=int(order_seed))
+    info = (ctypes.c_int32 * 3)()
+    _check(lib().mrip_mlp_train(int(d_in), _dev(x, t.float32, "x"), _dev(y, t.float32, "y"), n,
+                                _dev(xv, t.float32, allow_none=True),
+                                _dev(yv, t.float32, allow_none=True), n_val, ctypes.byref(prm),
+                                _dev(theta, t.float32, "theta"),
+                                _dev(losses, t.float32, allow_none=True),
+                                _dev(grad, t.float32, allow_none=True),
+                                _dev(m, t.float32, allow_none=True),
+                                _dev(v, t.float32, allow_none=True),
+                                _dev(val_losses, t.float32, allow_none=True), info,
+                                _stream(stream)))
+    return int(info[0]), int(info[1]), int(info[2])
+
+
 def mrip_cv_reduce(y, g, gc, out, stream=None):
     t = _t()
     _check(lib().mrip_cv_reduce(_dev(y, t.float64), _dev(g, t.float64), y.shape[1],
@@ -336,24 +362,36 @@ def mrip_autotune(model, design_points, n_reps, seed, trials=3, cache_path=None)
                                cache_path.encode() if cache_path else None))
 
 
-def mrip_run_cv(model, design_points, n_reps, seed, train_frac=0.1, epochs=20, batch=1024,
-                lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, m_ctrl=None, conf=0.95, net_seed=None):
+def mrip_run_cv(model, design_points, n_reps, seed, train_frac=0.1, val_frac=0.1, epochs=20,
+                patience=3, batch=1024, gate=True, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                m_ctrl=0, conf=0.95, net_seed=None):
+    """Returns (plain intervals, control-variate intervals, report dict);
+    m_ctrl = 0 lets the library size the control runs."""
     a, p = _host(design_points, np.float64)
     n_dp = a.shape[0]
-    if m_ctrl is None:
-        import math
-        n_train = math.ceil(train_frac * n_reps)
-        m_ctrl = 10 * (int(n_reps) - n_train)
-    prm = mrip_cv_params(train_frac=train_frac, epochs=epochs, batch=batch, lr=lr, beta1=beta1,
-                         beta2=beta2, eps=eps, m_ctrl=int(m_ctrl), conf=conf,
+    prm = mrip_cv_params(train_frac=train_frac, val_frac=val_frac, epochs=epochs, patience=patience,
+                         batch=batch, gate=1 if gate else 0, lr=lr, beta1=beta1, beta2=beta2,
+                         eps=eps, m_ctrl=int(m_ctrl or 0), conf=conf,
                          net_seed=int(seed if net_seed is None else net_seed))
     plain = (mrip_stat * n_dp)()
     cv = (mrip_cv_stat * n_dp)()
-    loss = ctypes.c_float()
+    rep = mrip_cv_report()
     _check(lib().mrip_run_cv(model, p, n_dp, int(n_reps), int(seed), ctypes.byref(prm), plain,
-                             cv, ctypes.byref(loss)))
+                             cv, ctypes.byref(rep)))
+    report = {name: getattr(rep, name) for name, _ in mrip_cv_report._fields_}
+    report["declined"] = bool(report["declined"])
     return [_stat_dict(plain[i]) for i in range(n_dp)], [_cv_dict(cv[i]) for i in range(n_dp)], \
-        loss.value
+        report
+
+
+def mrip_cv_network(model, d_in):
+    """(parameters float32[P], standardisation float64[d_in + 1][2]) of the
+    handle's last control-variate run."""
+    th = np.empty(mrip_mlp_param_count(d_in), dtype=np.float32)
+    norm = np.empty(2 * (d_in + 1))
+    _check(lib().mrip_cv_network(model, th.ctypes.data_as(ctypes.c_void_p),
+                                 norm.ctypes.data_as(ctypes.c_void_p)))
+    return th, norm.reshape(d_in + 1, 2)
 
 
 def mrip_destroy(model):
@@ -408,6 +446,9 @@ class Model:
 
     def run_cv(self, design_points, n_reps, seed, **kw):
         return mrip_run_cv(self.h, design_points, n_reps, seed, **kw)
+
+    def cv_network(self):
+        return mrip_cv_network(self.h, 8 if self.kind == MRIP_TANDEM3 else 6)
 
     def close(self):
         if self.h is not None:

@@ -50,11 +50,28 @@ class mrip_walk_params(ctypes.Structure):
     _fields_ = [("max_steps", ctypes.c_int64)]
 
 
+class mrip_train_params(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int32), ("patience", ctypes.c_int32),
+                ("max_steps", ctypes.c_int64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("order_seed", ctypes.c_uint64)]
+
+
 class mrip_cv_params(ctypes.Structure):
-    _fields_ = [("train_frac", ctypes.c_double), ("epochs", ctypes.c_int32),
-                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+    _fields_ = [("train_frac", ctypes.c_double), ("val_frac", ctypes.c_double),
+                ("epochs", ctypes.c_int32), ("patience", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("gate", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("m_ctrl", ctypes.c_int64),
                 ("conf", ctypes.c_double), ("net_seed", ctypes.c_uint64)]
+
+
+class mrip_cv_report(ctypes.Structure):
+    _fields_ = [("declined", ctypes.c_int32), ("epochs_run", ctypes.c_int32),
+                ("best_epoch", ctypes.c_int32), ("n_val", ctypes.c_int32),
+                ("m_ctrl", ctypes.c_int64), ("train_loss", ctypes.c_float),
+                ("val_loss", ctypes.c_float), ("val_rho2", ctypes.c_double),
+                ("var_ratio", ctypes.c_double), ("ms_simulate", ctypes.c_double),
+                ("ms_train", ctypes.c_double), ("ms_control", ctypes.c_double),
+                ("ms_infer", ctypes.c_double), ("ms_estimate", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -75,6 +92,7 @@ SIGNATURES = {
     "mrip_get_plan": (_INT, [_P, ctypes.c_char_p, _SZ]),
     "mrip_autotune": (_INT, [_P, _P, _I32, _I64, _U64, _INT, ctypes.c_char_p]),
     "mrip_run_cv": (_INT, [_P, _P, _I32, _I64, _U64, _P, _P, _P, _P]),
+    "mrip_cv_network": (_INT, [_P, _P, _P]),
     "mrip_destroy": (None, [_P]),
     "mrip_last_error": (ctypes.c_char_p, []),
     "mrip_philox": (_INT, [_P, _P, _I64, _P, _P]),
@@ -103,6 +121,8 @@ SIGNATURES = {
     "mrip_mlp_forward": (_INT, [_P, _I32, _P, _I64, _P, _P]),
     "mrip_mlp_loss_grad": (_INT, [_P, _I32, _P, _P, _I64, _P, _I64, _P, _P, _P]),
     "mrip_adam_step": (_INT, [_P, _P, _P, _P, _I64, _I64, _F, _F, _F, _F, _P]),
+    "mrip_mlp_train": (_INT, [_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
+                              _P]),
     "mrip_cv_reduce": (_INT, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
 }
 

@@ -639,10 +639,23 @@ extern "C" mrip_status mrip_autotune(mrip_model* m, const double* design_points,
 
 extern "C" mrip_status mrip_run_cv(mrip_model* m, const double* design_points, int32_t n_dp, int64_t n_reps,
                                    uint64_t seed, const mrip_cv_params* params, mrip_stat* plain_out,
-                                   mrip_cv_stat* cv_out, float* train_loss_out) {
+                                   mrip_cv_stat* cv_out, mrip_cv_report* report) {
     if (!m || !design_points || !params || !plain_out || !cv_out)
         return fail(MRIP_EINVAL, "mrip_run_cv: null argument");
-    return run_cv_impl(m, design_points, n_dp, n_reps, seed, params, plain_out, cv_out, train_loss_out);
+    return run_cv_impl(m, design_points, n_dp, n_reps, seed, params, plain_out, cv_out, report);
+}
+
+extern "C" mrip_status mrip_cv_network(mrip_model* m, float* theta_out, double* norm_out) {
+    if (!m) return fail(MRIP_EINVAL, "mrip_cv_network: null model");
+    if (m->cv_d_in == 0) return fail(MRIP_ESTATE, "mrip_cv_network: no mrip_run_cv yet");
+    if (theta_out) {
+        cudaError_t e = cudaMemcpyAsync(theta_out, m->cv_theta.p, mlp_params(m->cv_d_in) * sizeof(float),
+                                        cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_status(e, "mrip_cv_network");
+    }
+    if (norm_out) std::memcpy(norm_out, m->cv_norm.data(), m->cv_norm.size() * sizeof(double));
+    return MRIP_OK;
 }
 
 extern "C" void mrip_destroy(mrip_model* m) { delete m; }

@@ -5,16 +5,27 @@
 //      mu1..3 and the means of the first `window` gaps and services; forest
 //      fire: log10 p_grow, log10 p_lightning and the mean burning fraction of
 //      the four quarters of the first `window` steps) and its output Y;
-//   2. trains the network on the first ceil(train_frac n) replications of
-//      every design point with the engine's kernels (inputs and target
-//      standardised by the training set's FP64 mean and population std;
-//      Adam; epoch order pi(i) = (a i + b) mod n from stream tag 4);
-//   3. predicts g for the held-out replications and for m_ctrl control runs
-//      per design point -- replications n .. n + m_ctrl - 1 of the same
-//      streams, simulated only for the early window;
-//   4. reduces per design point: beta = Cov(Y, g)/Var(g),
+//   2. trains the network on the first n_fit of the n_train = ceil(train_frac
+//      n) training replications of every design point with the tensor-core
+//      kernel (inputs and target standardised by the fit set's FP64 mean and
+//      population std; Adam; epoch order pi(i) = (a i + b) mod n from stream
+//      tag 4), the other n_val = ceil(val_frac n_train) being the validation
+//      set of the early stop;
+//   3. estimates rho^2, the pooled within-design-point squared correlation
+//      of Y and the prediction g on the validation replications (each design
+//      point's deviations scaled by its fit-set standard deviations, so all
+//      design points weigh the same), sizes the
+//      control runs from it (the control mean may add a tenth to the
+//      residual variance) and, with the gate on, declines the control
+//      variate when its predicted variance at this n is not below the plain
+//      estimator's;
+//   4. predicts g for the held-out replications and for M control runs per
+//      design point -- replications n .. n + M - 1 of the same streams,
+//      simulated only for the early window;
+//   5. reduces per design point: beta = Cov(Y, g)/Var(g),
 //      Y_cv = mean(Y) - beta (mean(g) - mean(g_ctrl)),
-//      Var = s_r^2 / n + beta^2 Var(g_ctrl) / m, t on n - 2 degrees of freedom.
+//      Var = s_r^2 / n + beta^2 Var(g_ctrl) / M, t on n - 2 degrees of freedom.
+#include <algorithm>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -69,23 +80,83 @@ __global__ void to_double(const float* __restrict__ a, long long n, double* __re
     if (i < n) b[i] = static_cast<double>(a[i]);
 }
 
+// Per design point (one thread each): the within-design-point sums S_yg,
+// S_yy, S_gg of its n validation pairs (y, g) about their means, each
+// deviation divided by the design point's population standard deviation of
+// y (or g) over its n_fit fit replications, so that every design point
+// weighs the same whatever its variance; a design point whose fit y or g is
+// constant contributes nothing (FP64, two passes each).
+__global__ void within_dp_sums(const double* __restrict__ y, const double* __restrict__ g, long long n,
+                               const double* __restrict__ yf, const double* __restrict__ gf, long long n_fit,
+                               int n_dp, double* __restrict__ out) {
+    const int dp = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dp >= n_dp) return;
+    auto mean = [](const double* a, long long k) {
+        double s = 0.0;
+        for (long long i = 0; i < k; ++i) s += a[i];
+        return s / static_cast<double>(k);
+    };
+    auto pstd = [](const double* a, long long k, double m) {
+        double s = 0.0;
+        for (long long i = 0; i < k; ++i) s += (a[i] - m) * (a[i] - m);
+        return sqrt(s / static_cast<double>(k));
+    };
+    const double* yfr = yf + dp * n_fit;
+    const double* gfr = gf + dp * n_fit;
+    const double sy = pstd(yfr, n_fit, mean(yfr, n_fit)), sg = pstd(gfr, n_fit, mean(gfr, n_fit));
+    double syg = 0.0, syy = 0.0, sgg = 0.0;
+    if (sy > 0.0 && sg > 0.0) {
+        const double* yr = y + dp * n;
+        const double* gr = g + dp * n;
+        const double ym = mean(yr, n), gm = mean(gr, n);
+        for (long long i = 0; i < n; ++i) {
+            const double dy = (yr[i] - ym) / sy, dg = (gr[i] - gm) / sg;
+            syg += dy * dg;
+            syy += dy * dy;
+            sgg += dg * dg;
+        }
+    }
+    out[3 * dp] = syg;
+    out[3 * dp + 1] = syy;
+    out[3 * dp + 2] = sgg;
+}
+
 unsigned blocks(long long n) { return ceil_div_u(n, kT); }
 
-// Epoch order (a, b) for n samples: block (0, epoch) of tag 4, rep 0, dp 0.
-void epoch_affine(uint64_t seed, int epoch, unsigned long long n, unsigned long long& a, unsigned long long& b) {
-    if (n <= 1) {
-        a = 1;
-        b = 0;
-        return;
-    }
-    const uint4 w = philox(0u, static_cast<uint32_t>(epoch), 0u, stream_word(4u, 0u), expand_key(seed));
-    a = 1 + static_cast<unsigned long long>(w.x) % (n - 1);
-    while (std::gcd(a, n) != 1) {
-        ++a;
-        if (a >= n) a = 1;
-    }
-    b = static_cast<unsigned long long>(w.y) % n;
+// Control runs per design point for a pooled validation rho^2: the control
+// mean's term beta^2 Var(g_ctrl) / M ~ rho^2 sigma^2 / M at most a tenth of
+// the residual term (1 - rho^2) sigma^2 / n_held; [2, 100 n_held].
+long long control_runs(double rho2, long long n_held) {
+    if (!(rho2 >= 0.0)) return 10 * n_held;  // no validation: the fixed default
+    const double r = rho2 > 0.999999 ? 0.999999 : rho2;
+    double m = std::ceil(static_cast<double>(n_held) * r / (0.1 * (1.0 - r)));
+    const double cap = 100.0 * static_cast<double>(n_held);
+    if (m > cap) m = cap;
+    return m < 2.0 ? 2 : static_cast<long long>(m);
 }
+
+struct PhaseTimer {
+    cudaEvent_t ev[6] = {nullptr};
+    int n = 0;
+    cudaStream_t st;
+    explicit PhaseTimer(cudaStream_t s) : st(s) {
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    ~PhaseTimer() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void mark() {
+        if (n < 6) cudaEventRecord(ev[n++], st);
+    }
+    double ms(int a, int b) const {
+        if (b >= n) return 0.0;
+        float t = 0.0f;
+        cudaEventSynchronize(ev[b]);
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
 
 // Per-plane FP64 mean and population std (zero std -> 1) of d planes of n.
 mrip_status plane_moments(const double* x, int d, long long n, DevBuf& tmp, double* host_ms, double* dev_ms,
@@ -116,32 +187,48 @@ mrip_status plane_moments(const double* x, int d, long long n, DevBuf& tmp, doub
 }  // namespace
 
 mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t n_reps, uint64_t seed,
-                        const mrip_cv_params* p, mrip_stat* plain_out, mrip_cv_stat* cv_out, float* loss_out) {
+                        const mrip_cv_params* p, mrip_stat* plain_out, mrip_cv_stat* cv_out, mrip_cv_report* rep) {
     if (m->kind != MRIP_TANDEM3 && m->kind != MRIP_FOREST_FIRE)
         return fail(MRIP_EUNSUPPORTED, "mrip_run_cv: control variates exist for TANDEM3 and FOREST_FIRE");
-    if (!(p->train_frac > 0.0 && p->train_frac < 1.0) || p->epochs < 1 || p->batch < 1 || p->m_ctrl < 2 ||
+    if (!(p->train_frac > 0.0 && p->train_frac < 1.0) || !(p->val_frac >= 0.0 && p->val_frac < 1.0) ||
+        p->epochs < 1 || p->batch < 1 || p->patience < 0 || (p->m_ctrl != 0 && p->m_ctrl < 2) ||
         !(p->conf > 0.0 && p->conf < 1.0) || !(p->lr > 0.0f))
-        return fail(MRIP_EINVAL, "mrip_run_cv: train_frac in (0,1), epochs, batch >= 1, m_ctrl >= 2, conf in (0,1)");
+        return fail(MRIP_EINVAL, "mrip_run_cv: train_frac in (0,1), val_frac in [0,1), epochs, batch >= 1, "
+                                 "patience >= 0, m_ctrl 0 or >= 2, conf in (0,1)");
     const long long n_train = static_cast<long long>(std::ceil(p->train_frac * static_cast<double>(n_reps)));
     const long long n_held = n_reps - n_train;
-    if (n_train < 1 || n_held < 3) return fail(MRIP_EINVAL, "mrip_run_cv: need >= 1 training and >= 3 held-out replications");
-    if (n_reps + p->m_ctrl > 0x100000000ll) return fail(MRIP_EINVAL, "mrip_run_cv: replication indices < 2^32");
+    const long long n_val =
+        p->val_frac > 0.0 ? static_cast<long long>(std::ceil(p->val_frac * static_cast<double>(n_train))) : 0;
+    const long long n_fit = n_train - n_val;
+    if (n_fit < 1 || n_held < 3)
+        return fail(MRIP_EINVAL, "mrip_run_cv: need >= 1 fit and >= 3 held-out replications");
+    const long long m_cap = std::max<long long>(10 * n_held, 100 * n_held);
+    if (n_reps + std::max<long long>(p->m_ctrl, m_cap) > 0x100000000ll)
+        return fail(MRIP_EINVAL, "mrip_run_cv: replication indices < 2^32");
     const bool tandem = m->kind == MRIP_TANDEM3;
     const int d_in = tandem ? 8 : 6;
     const long long window = tandem ? m->tandem.window : m->ff.window;
     if (!tandem && window < 4) return fail(MRIP_EINVAL, "mrip_run_cv: forest-fire window must be >= 4 steps");
+    cudaStream_t st = m->stream;
+    PhaseTimer timer(st);
+    mrip_cv_report R{};
+    R.val_loss = std::nanf("");
+    R.val_rho2 = std::nan("");
+    R.var_ratio = std::nan("");
+    R.n_val = static_cast<int32_t>(n_val);
 
     // 1. plain run (the reference estimate and fallback) and its intervals
+    timer.mark();
     mrip_status s = mrip_run(m, dps, n_dp, n_reps, seed);
     if (s != MRIP_OK) return s;
     s = mrip_stats(m, p->conf, plain_out);
     if (s != MRIP_OK) return s;
-    cudaStream_t st = m->stream;
+    timer.mark();
     const long long items = static_cast<long long>(n_dp) * n_reps;
     const double cells = tandem ? 0.0 : static_cast<double>(m->ff.L) * m->ff.L;
 
-    DevBuf feat_all, y_all_ff, x_tr, y_tr, x_ho, y_ho, ms_dev, tmp, xs_tr, ys_tr, xs_ho, g_ho, g_hod, theta, sched,
-        losses, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
+    DevBuf feat_all, x_fit, y_fit, x_val, y_val, x_ho, y_ho, ms_dev, tmp, xs_fit, ys_fit, xs_val, ys_val, xs_ho,
+        g_val, g_vald, g_fit, g_fitd, g_ho, g_hod, losses, val_losses, wsums, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
     const double* feat_src;  // d_in planes of `items`
     const double* y_src;     // items
     if (tandem) {
@@ -158,88 +245,163 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
         y_src = m->out1.as<double>();
     }
 
-    // 2. training and held-out sets
-    const long long n_tr = static_cast<long long>(n_dp) * n_train;
+    // 2. fit, validation and held-out sets (replications [0, n_fit), [n_fit,
+    //    n_train), [n_train, n_reps) of every design point)
+    const long long n_f = static_cast<long long>(n_dp) * n_fit;
+    const long long n_v = static_cast<long long>(n_dp) * n_val;
     const long long n_ho = static_cast<long long>(n_dp) * n_held;
-    if (!x_tr.ensure(d_in * n_tr * sizeof(double)) || !y_tr.ensure(n_tr * sizeof(double)) ||
+    if (!x_fit.ensure(d_in * n_f * sizeof(double)) || !y_fit.ensure(n_f * sizeof(double)) ||
+        !xs_fit.ensure(d_in * n_f * sizeof(float)) || !ys_fit.ensure(n_f * sizeof(float)) ||
         !x_ho.ensure(d_in * n_ho * sizeof(double)) || !y_ho.ensure(n_ho * sizeof(double)) ||
-        !xs_tr.ensure(d_in * n_tr * sizeof(float)) || !ys_tr.ensure(n_tr * sizeof(float)) ||
         !xs_ho.ensure(d_in * n_ho * sizeof(float)) || !g_ho.ensure(n_ho * sizeof(float)) ||
         !g_hod.ensure(n_ho * sizeof(double)) || !ms_dev.ensure(2 * (d_in + 1) * sizeof(double)))
         return fail(MRIP_ENOMEM, "cv: training buffers");
-    gather_planes<<<blocks(n_tr), kT, 0, st>>>(feat_src, items, d_in, n_reps, 0, n_train, n_tr, x_tr.as<double>());
-    gather_planes<<<blocks(n_tr), kT, 0, st>>>(y_src, items, 1, n_reps, 0, n_train, n_tr, y_tr.as<double>());
+    if (n_v > 0 && (!x_val.ensure(d_in * n_v * sizeof(double)) || !y_val.ensure(n_v * sizeof(double)) ||
+                    !xs_val.ensure(d_in * n_v * sizeof(float)) || !ys_val.ensure(n_v * sizeof(float)) ||
+                    !g_val.ensure(n_v * sizeof(float)) || !g_vald.ensure(n_v * sizeof(double)) ||
+                    !wsums.ensure(3 * static_cast<size_t>(n_dp) * sizeof(double))))
+        return fail(MRIP_ENOMEM, "cv: validation buffers");
+    gather_planes<<<blocks(n_f), kT, 0, st>>>(feat_src, items, d_in, n_reps, 0, n_fit, n_f, x_fit.as<double>());
+    gather_planes<<<blocks(n_f), kT, 0, st>>>(y_src, items, 1, n_reps, 0, n_fit, n_f, y_fit.as<double>());
     gather_planes<<<blocks(n_ho), kT, 0, st>>>(feat_src, items, d_in, n_reps, n_train, n_held, n_ho, x_ho.as<double>());
     gather_planes<<<blocks(n_ho), kT, 0, st>>>(y_src, items, 1, n_reps, n_train, n_held, n_ho, y_ho.as<double>());
+    if (n_v > 0) {
+        gather_planes<<<blocks(n_v), kT, 0, st>>>(feat_src, items, d_in, n_reps, n_fit, n_val, n_v,
+                                                  x_val.as<double>());
+        gather_planes<<<blocks(n_v), kT, 0, st>>>(y_src, items, 1, n_reps, n_fit, n_val, n_v, y_val.as<double>());
+    }
     s = launch_status("cv: gather");
     if (s != MRIP_OK) return s;
     std::vector<double> ms(2 * (d_in + 1));
-    s = plane_moments(x_tr.as<double>(), d_in, n_tr, tmp, ms.data(), ms_dev.as<double>(), st);
+    s = plane_moments(x_fit.as<double>(), d_in, n_f, tmp, ms.data(), ms_dev.as<double>(), st);
     if (s != MRIP_OK) return s;
-    s = plane_moments(y_tr.as<double>(), 1, n_tr, tmp, ms.data() + 2 * d_in, ms_dev.as<double>() + 2 * d_in, st);
+    s = plane_moments(y_fit.as<double>(), 1, n_f, tmp, ms.data() + 2 * d_in, ms_dev.as<double>() + 2 * d_in, st);
     if (s != MRIP_OK) return s;
-    standardize<<<blocks(n_tr), kT, 0, st>>>(x_tr.as<double>(), n_tr, d_in, ms_dev.as<double>(), xs_tr.as<float>());
-    standardize<<<blocks(n_tr), kT, 0, st>>>(y_tr.as<double>(), n_tr, 1, ms_dev.as<double>() + 2 * d_in,
-                                             ys_tr.as<float>());
-    standardize<<<blocks(n_ho), kT, 0, st>>>(x_ho.as<double>(), n_ho, d_in, ms_dev.as<double>(), xs_ho.as<float>());
+    const double* d_ms = ms_dev.as<double>();
+    standardize<<<blocks(n_f), kT, 0, st>>>(x_fit.as<double>(), n_f, d_in, d_ms, xs_fit.as<float>());
+    standardize<<<blocks(n_f), kT, 0, st>>>(y_fit.as<double>(), n_f, 1, d_ms + 2 * d_in, ys_fit.as<float>());
+    standardize<<<blocks(n_ho), kT, 0, st>>>(x_ho.as<double>(), n_ho, d_in, d_ms, xs_ho.as<float>());
+    if (n_v > 0) {
+        standardize<<<blocks(n_v), kT, 0, st>>>(x_val.as<double>(), n_v, d_in, d_ms, xs_val.as<float>());
+        standardize<<<blocks(n_v), kT, 0, st>>>(y_val.as<double>(), n_v, 1, d_ms + 2 * d_in, ys_val.as<float>());
+    }
     s = launch_status("cv: standardise");
     if (s != MRIP_OK) return s;
 
-    // 3. training
+    // 3. training (early stop on the validation set), validation rho^2
     const long long P = mlp_params(d_in);
     const long long B = p->batch;
-    const long long steps_per_epoch = (n_tr + B - 1) / B;
-    const long long n_steps = steps_per_epoch * p->epochs;
-    // per epoch the affine order (a, b), per step Adam's bias corrections,
-    // computed here in double and rounded to float as the stage entry points
-    // take them; then all epochs in one cluster launch
-    std::vector<unsigned long long> ab(2 * static_cast<size_t>(p->epochs));
-    for (int ep = 0; ep < p->epochs; ++ep)
-        epoch_affine(p->net_seed, ep, static_cast<unsigned long long>(n_tr), ab[2 * ep], ab[2 * ep + 1]);
-    std::vector<float> bc(2 * static_cast<size_t>(n_steps));
-    for (long long k = 1; k <= n_steps; ++k) {
-        bc[2 * (k - 1)] = static_cast<float>(1.0 - std::pow(static_cast<double>(p->beta1), static_cast<double>(k)));
-        bc[2 * (k - 1) + 1] =
-            static_cast<float>(1.0 - std::pow(static_cast<double>(p->beta2), static_cast<double>(k)));
-    }
-    const size_t ab_bytes = ab.size() * sizeof(unsigned long long);
-    if (!theta.ensure(P * sizeof(float)) || !losses.ensure(n_steps * sizeof(float)) ||
-        !sched.ensure(ab_bytes + bc.size() * sizeof(float)))
+    const long long spe = (n_f + B - 1) / B;
+    const long long n_steps = spe * p->epochs;
+    if (!m->cv_theta.ensure(P * sizeof(float)) || !losses.ensure(n_steps * sizeof(float)) ||
+        !val_losses.ensure(static_cast<size_t>(p->epochs) * sizeof(float)))
         return fail(MRIP_ENOMEM, "cv: network buffers");
-    cudaError_t e = cudaMemcpyAsync(sched.p, ab.data(), ab_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(static_cast<char*>(sched.p) + ab_bytes, bc.data(), bc.size() * sizeof(float),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
-    if (e != cudaSuccess) return cuda_status(e, "cv: training schedule");
-    s = mlp_init(d_in, p->net_seed, theta.as<float>(), st);
+    float* theta = m->cv_theta.as<float>();
+    m->cv_d_in = 0;  // valid again once training succeeded
+    s = mlp_init(d_in, p->net_seed, theta, st);
     if (s != MRIP_OK) return s;
-    s = mlp_train_tc(d_in, xs_tr.as<float>(), ys_tr.as<float>(), n_tr, B, p->epochs, sched.as<unsigned long long>(),
-                  reinterpret_cast<const float*>(static_cast<char*>(sched.p) + ab_bytes), p->lr, p->beta1,
-                  p->beta2, p->eps, theta.as<float>(), losses.as<float>(), st);
+    TrainSpec sp{};
+    sp.d_in = d_in;
+    sp.X = xs_fit.as<float>();
+    sp.Y = ys_fit.as<float>();
+    sp.n = n_f;
+    sp.Xv = n_v > 0 ? xs_val.as<float>() : nullptr;
+    sp.Yv = n_v > 0 ? ys_val.as<float>() : nullptr;
+    sp.n_val = n_v;
+    sp.B = B;
+    sp.epochs = p->epochs;
+    sp.patience = p->patience;
+    sp.order_seed = p->net_seed;
+    sp.lr = p->lr;
+    sp.beta1 = p->beta1;
+    sp.beta2 = p->beta2;
+    sp.eps = p->eps;
+    sp.theta = theta;
+    sp.losses = losses.as<float>();
+    sp.val_losses = n_v > 0 ? val_losses.as<float>() : nullptr;
+    TrainInfo info{};
+    s = mlp_train(sp, &info, st);
     if (s != MRIP_OK) return s;
-    if (loss_out) {
-        std::vector<float> hl(steps_per_epoch);
-        e = cudaMemcpyAsync(hl.data(), losses.as<float>() + (n_steps - steps_per_epoch),
-                            steps_per_epoch * sizeof(float), cudaMemcpyDeviceToHost, st);
+    m->cv_d_in = d_in;
+    m->cv_norm = ms;
+    R.epochs_run = info.epochs_run;
+    R.best_epoch = info.best_epoch;
+    {   // mean minibatch loss of the last epoch run, and the kept epoch's validation loss
+        const long long last = static_cast<long long>(info.epochs_run > 0 ? info.epochs_run - 1 : 0) * spe;
+        std::vector<float> hl(spe);
+        cudaError_t e = cudaMemcpyAsync(hl.data(), losses.as<float>() + last, spe * sizeof(float),
+                                        cudaMemcpyDeviceToHost, st);
+        float vl = std::nanf("");
+        if (e == cudaSuccess && n_v > 0 && info.best_epoch > 0)
+            e = cudaMemcpyAsync(&vl, val_losses.as<float>() + (info.best_epoch - 1), sizeof(float),
+                                cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(e, "cv: loss read");
         double acc = 0.0, wsum = 0.0;
-        for (long long k = 0; k < steps_per_epoch; ++k) {
-            const double w = static_cast<double>((k + 1) * B <= n_tr ? B : n_tr - k * B);
+        for (long long k = 0; k < spe; ++k) {
+            const double w = static_cast<double>((k + 1) * B <= n_f ? B : n_f - k * B);
             acc += w * hl[k];
             wsum += w;
         }
-        *loss_out = static_cast<float>(acc / wsum);
+        R.train_loss = static_cast<float>(acc / wsum);
+        R.val_loss = vl;
     }
+    double rho2 = std::nan("");
+    if (n_v > 0 && n_val >= 2) {
+        // predictions of the validation and fit replications (the fit set
+        // gives each design point's scales)
+        if (!g_fit.ensure(n_f * sizeof(float)) || !g_fitd.ensure(n_f * sizeof(double)))
+            return fail(MRIP_ENOMEM, "cv: fit predictions");
+        s = mlp_forward(theta, d_in, xs_val.as<float>(), n_v, g_val.as<float>(), st);
+        if (s == MRIP_OK) s = mlp_forward(theta, d_in, xs_fit.as<float>(), n_f, g_fit.as<float>(), st);
+        if (s != MRIP_OK) return s;
+        to_double<<<blocks(n_v), kT, 0, st>>>(g_val.as<float>(), n_v, g_vald.as<double>());
+        to_double<<<blocks(n_f), kT, 0, st>>>(g_fit.as<float>(), n_f, g_fitd.as<double>());
+        within_dp_sums<<<ceil_div_u(n_dp, 128), 128, 0, st>>>(y_val.as<double>(), g_vald.as<double>(), n_val,
+                                                             y_fit.as<double>(), g_fitd.as<double>(), n_fit,
+                                                             n_dp, wsums.as<double>());
+        s = launch_status("cv: validation correlation");
+        if (s != MRIP_OK) return s;
+        std::vector<double> h(3 * static_cast<size_t>(n_dp));
+        cudaError_t e = cudaMemcpyAsync(h.data(), wsums.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e, "cv: validation correlation");
+        double syg = 0.0, syy = 0.0, sgg = 0.0;
+        for (int32_t d = 0; d < n_dp; ++d) {  // design points in order
+            syg += h[3 * d];
+            syy += h[3 * d + 1];
+            sgg += h[3 * d + 2];
+        }
+        rho2 = (syy > 0.0 && sgg > 0.0) ? (syg * syg) / (syy * sgg) : 0.0;
+    }
+    R.val_rho2 = rho2;
+    const long long M = p->m_ctrl > 0 ? p->m_ctrl : control_runs(rho2, n_held);
+    if (rho2 >= 0.0)
+        R.var_ratio = static_cast<double>(n_reps) *
+                      ((1.0 - rho2) / static_cast<double>(n_held) + rho2 / static_cast<double>(M));
+    timer.mark();
 
-    // 4. held-out predictions
-    s = mlp_forward(theta.as<float>(), d_in, xs_ho.as<float>(), n_ho, g_ho.as<float>(), st);
-    if (s != MRIP_OK) return s;
-    to_double<<<blocks(n_ho), kT, 0, st>>>(g_ho.as<float>(), n_ho, g_hod.as<double>());
+    if (p->gate && R.var_ratio >= 1.0) {  // the plain estimator stays
+        R.declined = 1;
+        R.m_ctrl = 0;
+        for (int32_t d = 0; d < n_dp; ++d) {
+            mrip_cv_stat& o = cv_out[d];
+            o.n = plain_out[d].n;
+            o.m = 0;
+            o.beta = 0.0;
+            o.mean = plain_out[d].mean;
+            o.var = plain_out[d].var / static_cast<double>(plain_out[d].n);
+            o.half_width = plain_out[d].half_width;
+            o.t_crit = plain_out[d].t_crit;
+        }
+        R.ms_simulate = timer.ms(0, 1);
+        R.ms_train = timer.ms(1, 2);
+        if (rep) *rep = R;
+        return MRIP_OK;
+    }
+    R.m_ctrl = M;
 
-    // 5. control runs: replications n_reps .. n_reps + m_ctrl - 1, early window only
-    const long long M = p->m_ctrl;
+    // 4. control runs: replications n_reps .. n_reps + M - 1, early window only
     const long long n_c = static_cast<long long>(n_dp) * M;
     if (!c_feat.ensure(d_in * n_c * sizeof(double)) || !c_y.ensure(n_c * sizeof(double)) ||
         !xs_c.ensure(d_in * n_c * sizeof(float)) || !g_c.ensure(n_c * sizeof(float)) ||
@@ -261,16 +423,27 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
         }
     }
     if (s != MRIP_OK) return s;
-    standardize<<<blocks(n_c), kT, 0, st>>>(c_feat.as<double>(), n_c, d_in, ms_dev.as<double>(), xs_c.as<float>());
-    s = mlp_forward(theta.as<float>(), d_in, xs_c.as<float>(), n_c, g_c.as<float>(), st);
+    standardize<<<blocks(n_c), kT, 0, st>>>(c_feat.as<double>(), n_c, d_in, d_ms, xs_c.as<float>());
+    s = launch_status("cv: control standardise");
     if (s != MRIP_OK) return s;
-    to_double<<<blocks(n_c), kT, 0, st>>>(g_c.as<float>(), n_c, g_cd.as<double>());
+    timer.mark();
 
-    // 6. per-design-point estimator
+    // predictions of the held-out replications and the control runs
+    s = mlp_forward(theta, d_in, xs_ho.as<float>(), n_ho, g_ho.as<float>(), st);
+    if (s != MRIP_OK) return s;
+    s = mlp_forward(theta, d_in, xs_c.as<float>(), n_c, g_c.as<float>(), st);
+    if (s != MRIP_OK) return s;
+    to_double<<<blocks(n_ho), kT, 0, st>>>(g_ho.as<float>(), n_ho, g_hod.as<double>());
+    to_double<<<blocks(n_c), kT, 0, st>>>(g_c.as<float>(), n_c, g_cd.as<double>());
+    s = launch_status("cv: predictions");
+    if (s != MRIP_OK) return s;
+    timer.mark();
+
+    // 5. per-design-point estimator
     s = cv_reduce(y_ho.as<double>(), g_hod.as<double>(), n_held, g_cd.as<double>(), M, n_dp, out5.as<double>(), st);
     if (s != MRIP_OK) return s;
     std::vector<double> h(5 * static_cast<size_t>(n_dp));
-    e = cudaMemcpyAsync(h.data(), out5.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(h.data(), out5.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e, "cv: result read");
     const double tc = t_critical(p->conf, n_held - 2);
@@ -284,6 +457,13 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
         o.t_crit = tc;
         o.half_width = tc * std::sqrt(o.var);
     }
+    timer.mark();
+    R.ms_simulate = timer.ms(0, 1);
+    R.ms_train = timer.ms(1, 2);
+    R.ms_control = timer.ms(2, 3);
+    R.ms_infer = timer.ms(3, 4);
+    R.ms_estimate = timer.ms(4, 5);
+    if (rep) *rep = R;
     return MRIP_OK;
 }
 

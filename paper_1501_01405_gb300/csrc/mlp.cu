@@ -23,6 +23,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <numeric>
+#include <vector>
 
 #include "common.cuh"
 #include "model.cuh"
@@ -372,8 +374,18 @@ struct TrainArgs {
     const unsigned long long* ab;  // per epoch: the affine order (a, b)
     const float* bc;               // per step: the bias corrections (1 - beta1^t, 1 - beta2^t)
     float lr, beta1, beta2, eps;
-    float* theta;   // in: initial parameters; out: trained
-    float* losses;  // per step: mean squared residual of the minibatch
+    float* theta;   // in: initial parameters; out: trained (the best epoch's with validation)
+    float* losses;  // per step: mean squared residual of the minibatch (may be null)
+    long long max_steps;  // > 0: stop after this many steps
+    float* grad;    // may be null: the gradient of the last step
+    float* m_out;   // may be null: Adam's first moment after the last step
+    float* v_out;   // may be null: Adam's second moment after the last step
+    const float* Xv;  // validation features, d_in planes of n_val (n_val = 0: none)
+    const float* Yv;
+    long long n_val;
+    int patience;       // > 0: stop after this many epochs without a lower validation loss
+    float* val_losses;  // per epoch (may be null)
+    int* info;          // may be null: epochs run, epoch kept, steps run
 };
 
 // ---------------------------------------------------------------------------
@@ -489,94 +501,113 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
         __syncthreads();
         tc::fence_after_sync();
     };
+    // BF16 operands (and FP32 biases) of the current parameters th
+    auto stage_weights = [&]() {
+        for (int i = t; i < H * 16; i += kTcThreads) {
+            const int u = i >> 4, k = i & 15;
+            put_bf16(S.w1b, tc::core_offset(u, k, 16), k < d_in ? theta_w1(th, d_in, u, k) : 0.0f);
+        }
+        for (int i = t; i < H * H; i += kTcThreads) {
+            const int v = i / H, u = i - v * H;
+            const float w = th[off_w2(d_in) + i];
+            put_bf16(S.w2b, tc::core_offset(v, u, H), w);
+            put_bf16(S.w2tb, tc::core_offset(u, v, H), w);
+        }
+        for (int i = t; i < H; i += kTcThreads) {
+            S.w3[i] = bf(th[off_w3(d_in) + i]);
+            S.b1[i] = th[off_b1(d_in) + i];
+            S.b2[i] = th[off_b2(d_in) + i];
+        }
+        if (t == 0) S.b3 = th[off_b3(d_in)];
+    };
+    // Forward pass of one tile: row m is sample smp of the planes Xs (n_total
+    // samples each) when valid, else zero.  Leaves H1~ (rows and transposed),
+    // H2~ rows and X~ in shared memory and the ReLU masks of this thread's 16
+    // columns in mask1 / mask2; returns the output of row m without b3.
+    auto forward_tile = [&](const float* Xs, long long n_total, long long smp, bool valid, uint32_t& mask1,
+                            uint32_t& mask2) -> float {
+        for (int k = 2 * cb; k < 2 * cb + 2; ++k) {  // features 2cb, 2cb + 1 of row m
+            const float x = (valid && k < d_in) ? bf(Xs[k * n_total + smp]) : 0.0f;
+            S.xs[m][k] = x;
+            if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
+        }
+        sync_for_mma();
+        if (t == 0 && ok) {
+            tc::mma_bf16(tm, tc::smem_desc(tc::smem_addr(S.a1), 128, 256),
+                         tc::smem_desc(tc::smem_addr(S.w1b), 128, 256), kIdesc, false);
+            tc::mma_commit(&S.bar);
+        }
+        wait_mma();
+        // layer 1 epilogue: h1 = relu(z1 + b1) on columns c0 .. c0 + 15
+        mask1 = 0u;
+        {
+            float z[16];
+            tc::tmem_ld16(tm + lane_base + c0, z);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int u = c0 + j;
+                const float h = fmaxf(z[j] + S.b1[u], 0.0f);
+                if (h > 0.0f) mask1 |= 1u << j;
+                const float hb = bf(h);
+                put_bf16(S.a2, tc::core_offset(m, u, H), hb);
+                put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), hb);
+            }
+        }
+        sync_for_mma();
+        if (t == 0 && ok) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                tc::mma_bf16(tm + 64, tc::smem_desc(tc::smem_addr(S.a2) + 256 * ks, 128, 1024),
+                             tc::smem_desc(tc::smem_addr(S.w2b) + 256 * ks, 128, 1024), kIdesc, ks > 0);
+            tc::mma_commit(&S.bar);
+        }
+        wait_mma();
+        // layer 2 epilogue: h2 and this block's share of the output
+        mask2 = 0u;
+        {
+            float z[16], yp = 0.0f;
+            tc::tmem_ld16(tm + lane_base + 64 + c0, z);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int v = c0 + j;
+                const float h = fmaxf(z[j] + S.b2[v], 0.0f);
+                if (h > 0.0f) mask2 |= 1u << j;
+                const float hb = bf(h);
+                S.h2t[m][v] = __float2bfloat16_rn(hb);
+                yp = fmaf(hb, S.w3[v], yp);
+            }
+            S.ypart[cb][m] = yp;
+        }
+        __syncthreads();
+        return ((S.ypart[0][m] + S.ypart[1][m]) + S.ypart[2][m]) + S.ypart[3][m];
+    };
 
     long long step = 0;
-    for (int ep = 0; ep < ta.epochs; ++ep) {
+    bool stop = false;
+    float best = __int_as_float(0x7f800000);  // +inf
+    int bad = 0, best_epoch = 0, epochs_run = 0;
+    for (int ep = 0; ep < ta.epochs && !stop; ++ep) {
         const SampleMap map{nullptr, ta.ab[2 * ep], ta.ab[2 * ep + 1], static_cast<unsigned long long>(ta.n_tr), 0};
         for (long long off = 0; off < ta.n_tr; off += ta.B, ++step) {
+            if (ta.max_steps > 0 && step >= ta.max_steps) {  // uniform across the cluster
+                stop = true;
+                break;
+            }
             const long long nb = (off + ta.B <= ta.n_tr) ? ta.B : ta.n_tr - off;
             const long long chunk = (nb + kTcCluster - 1) / kTcCluster;
             const long long lo = min(nb, rank * chunk), hi = min(nb, lo + chunk);
             SampleMap smap = map;
             smap.off = off;
-            // BF16 operands of this step's weights
-            for (int i = t; i < H * 16; i += kTcThreads) {
-                const int u = i >> 4, k = i & 15;
-                put_bf16(S.w1b, tc::core_offset(u, k, 16), k < d_in ? theta_w1(th, d_in, u, k) : 0.0f);
-            }
-            for (int i = t; i < H * H; i += kTcThreads) {
-                const int v = i / H, u = i - v * H;
-                const float w = th[off_w2(d_in) + i];
-                put_bf16(S.w2b, tc::core_offset(v, u, H), w);
-                put_bf16(S.w2tb, tc::core_offset(u, v, H), w);
-            }
-            for (int i = t; i < H; i += kTcThreads) {
-                S.w3[i] = bf(th[off_w3(d_in) + i]);
-                S.b1[i] = th[off_b1(d_in) + i];
-                S.b2[i] = th[off_b2(d_in) + i];
-            }
-            if (t == 0) S.b3 = th[off_b3(d_in)];
+            stage_weights();
             for (int i = t; i <= P; i += kTcThreads) part[i] = 0.0f;
 
             for (long long p0 = lo; p0 < hi; p0 += kTcRows) {
                 const int n_valid = static_cast<int>(min(static_cast<long long>(kTcRows), hi - p0));
                 const bool valid = m < n_valid;
                 const long long smp = valid ? sample_of(smap, p0 + m) : 0;
-                for (int k = 2 * cb; k < 2 * cb + 2; ++k) {  // features 2cb, 2cb + 1 of row m
-                    const float x = (valid && k < d_in) ? bf(ta.X[k * ta.n_tr + smp]) : 0.0f;
-                    S.xs[m][k] = x;
-                    if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
-                }
                 const float y = valid ? ta.Y[smp] : 0.0f;
-                sync_for_mma();
-                if (t == 0 && ok) {
-                    tc::mma_bf16(tm, tc::smem_desc(tc::smem_addr(S.a1), 128, 256),
-                                 tc::smem_desc(tc::smem_addr(S.w1b), 128, 256), kIdesc, false);
-                    tc::mma_commit(&S.bar);
-                }
-                wait_mma();
-                // layer 1 epilogue: h1 = relu(z1 + b1) on columns c0 .. c0 + 15
-                uint32_t mask1 = 0u;
-                {
-                    float z[16];
-                    tc::tmem_ld16(tm + lane_base + c0, z);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int u = c0 + j;
-                        const float h = fmaxf(z[j] + S.b1[u], 0.0f);
-                        if (h > 0.0f) mask1 |= 1u << j;
-                        const float hb = bf(h);
-                        put_bf16(S.a2, tc::core_offset(m, u, H), hb);
-                        put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), hb);
-                    }
-                }
-                sync_for_mma();
-                if (t == 0 && ok) {
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks)
-                        tc::mma_bf16(tm + 64, tc::smem_desc(tc::smem_addr(S.a2) + 256 * ks, 128, 1024),
-                                     tc::smem_desc(tc::smem_addr(S.w2b) + 256 * ks, 128, 1024), kIdesc, ks > 0);
-                    tc::mma_commit(&S.bar);
-                }
-                wait_mma();
-                // layer 2 epilogue: h2 and this block's share of the output
-                uint32_t mask2 = 0u;
-                {
-                    float z[16], yp = 0.0f;
-                    tc::tmem_ld16(tm + lane_base + 64 + c0, z);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int v = c0 + j;
-                        const float h = fmaxf(z[j] + S.b2[v], 0.0f);
-                        if (h > 0.0f) mask2 |= 1u << j;
-                        const float hb = bf(h);
-                        S.h2t[m][v] = __float2bfloat16_rn(hb);
-                        yp = fmaf(hb, S.w3[v], yp);
-                    }
-                    S.ypart[cb][m] = yp;
-                }
-                __syncthreads();
-                const float yhat = ((S.ypart[0][m] + S.ypart[1][m]) + S.ypart[2][m]) + S.ypart[3][m];
+                uint32_t mask1, mask2;
+                const float yhat = forward_tile(ta.X, ta.n_tr, smp, valid, mask1, mask2);
                 const float r = valid ? (yhat + S.b3) - y : 0.0f;
                 const float dyv = valid ? 2.0f * r / static_cast<float>(nb) : 0.0f;
                 if (cb == 0) {
@@ -675,6 +706,7 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
             for (int p = p_lo + t; p < p_hi; p += kTcThreads) {
                 float g = 0.0f;
                 for (int rr = 0; rr < kTcCluster; ++rr) g += cluster.map_shared_rank(part, rr)[p];
+                if (ta.grad) ta.grad[p] = g;
                 const int q = p - p_lo;
                 const float mi = ta.beta1 * mom[q] + (1.0f - ta.beta1) * g;
                 const float vi = ta.beta2 * vel[q] + (1.0f - ta.beta2) * g * g;
@@ -686,12 +718,65 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
             if (rank == 0 && t == 0) {
                 float l = 0.0f;
                 for (int rr = 0; rr < kTcCluster; ++rr) l += cluster.map_shared_rank(part, rr)[P];
-                ta.losses[step] = l / static_cast<float>(nb);
+                if (ta.losses) ta.losses[step] = l / static_cast<float>(nb);
             }
             cluster.sync();
         }
+        if (stop) break;
+        ++epochs_run;
+        if (ta.n_val > 0) {
+            // validation loss of this epoch's parameters (each CTA a slice of
+            // the validation samples, in order; the CTAs' sums added in rank
+            // order, so every CTA computes the same value and takes the same
+            // early-stopping decision)
+            stage_weights();
+            if (t == 0) part[P] = 0.0f;
+            __syncthreads();
+            const long long vchunk = (ta.n_val + kTcCluster - 1) / kTcCluster;
+            const long long vlo = min(ta.n_val, rank * vchunk), vhi = min(ta.n_val, vlo + vchunk);
+            for (long long p0 = vlo; p0 < vhi; p0 += kTcRows) {
+                const int n_valid = static_cast<int>(min(static_cast<long long>(kTcRows), vhi - p0));
+                const bool valid = m < n_valid;
+                const long long smp = valid ? p0 + m : 0;
+                uint32_t mask1, mask2;
+                const float yhat = forward_tile(ta.Xv, ta.n_val, smp, valid, mask1, mask2);
+                const float r = valid ? (yhat + S.b3) - ta.Yv[smp] : 0.0f;
+                if (cb == 0) S.r2[m] = r * r;
+                __syncthreads();
+                if (t == H) {
+                    float l = 0.0f;
+                    for (int q = 0; q < kTcRows; ++q) l += S.r2[q];
+                    part[P] += l;
+                }
+                __syncthreads();
+            }
+            cluster.sync();
+            float vl = 0.0f;
+            for (int rr = 0; rr < kTcCluster; ++rr) vl += cluster.map_shared_rank(part, rr)[P];
+            vl /= static_cast<float>(ta.n_val);
+            cluster.sync();  // every CTA has read the sums before part[] is cleared again
+            if (rank == 0 && t == 0 && ta.val_losses) ta.val_losses[ep] = vl;
+            if (vl < best) {
+                best = vl;
+                best_epoch = ep + 1;
+                bad = 0;
+                for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta[p] = th[p];
+            } else if (ta.patience > 0 && ++bad >= ta.patience) {
+                stop = true;
+            }
+        }
     }
-    for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta[p] = th[p];
+    if (ta.n_val == 0)
+        for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta[p] = th[p];
+    if (ta.m_out)
+        for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.m_out[p] = mom[p - p_lo];
+    if (ta.v_out)
+        for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.v_out[p] = vel[p - p_lo];
+    if (rank == 0 && t == 0 && ta.info) {
+        ta.info[0] = epochs_run;
+        ta.info[1] = ta.n_val > 0 ? best_epoch : epochs_run;
+        ta.info[2] = static_cast<int>(step);
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -865,33 +950,78 @@ mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long 
     return launch_status("mlp reduce");
 }
 
-__device__ int g_tc_timeout;
+// Epoch order (a, b) of n samples: block (0, epoch) of tag 4, rep 0, dp 0;
+// a = 1 + w0 mod (n - 1) stepped up to the first value coprime with n,
+// b = w1 mod n.
+void epoch_affine(uint64_t seed, int epoch, unsigned long long n, unsigned long long& a, unsigned long long& b) {
+    if (n <= 1) {
+        a = 1;
+        b = 0;
+        return;
+    }
+    const uint4 w = philox(0u, static_cast<uint32_t>(epoch), 0u, stream_word(4u, 0u), expand_key(seed));
+    a = 1 + static_cast<unsigned long long>(w.x) % (n - 1);
+    while (std::gcd(a, n) != 1) {
+        ++a;
+        if (a >= n) a = 1;
+    }
+    b = static_cast<unsigned long long>(w.y) % n;
+}
 
-// All epochs of Adam training in one cluster launch with the contractions on
-// the tensor cores (mlp_train_tc_kernel).  Synchronous: reads back whether an
-// MMA completion wait ran out.
-mrip_status mlp_train_tc(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
-                         const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
-                         float eps, float* theta, float* losses, cudaStream_t st) {
-    if (n_tr == 0 || epochs == 0) return MRIP_OK;
-    const size_t smem = mlp_train_tc_smem(d_in);
-    cudaError_t e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+// Adam training in one cluster launch with the contractions on the tensor
+// cores (mlp_train_tc_kernel).  The host computes the schedule -- per epoch
+// the affine order, per step Adam's bias corrections in double rounded to
+// float -- and uploads it to library scratch.  Synchronous: reads back
+// whether an MMA completion wait ran out, and the run's counts.
+mrip_status mlp_train(const TrainSpec& sp, TrainInfo* info, cudaStream_t st) {
+    TrainInfo none{0, 0, 0};
+    if (info) *info = none;
+    if (sp.n == 0 || sp.epochs == 0) return MRIP_OK;
+    const long long spe = (sp.n + sp.B - 1) / sp.B;
+    long long n_steps = spe * sp.epochs;
+    if (sp.max_steps > 0 && sp.max_steps < n_steps) n_steps = sp.max_steps;
+    std::vector<unsigned long long> ab(2 * static_cast<size_t>(sp.epochs));
+    for (int ep = 0; ep < sp.epochs; ++ep)
+        epoch_affine(sp.order_seed, ep, static_cast<unsigned long long>(sp.n), ab[2 * ep], ab[2 * ep + 1]);
+    std::vector<float> bc(2 * static_cast<size_t>(n_steps));
+    for (long long k = 1; k <= n_steps; ++k) {
+        bc[2 * (k - 1)] = static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta1), static_cast<double>(k)));
+        bc[2 * (k - 1) + 1] =
+            static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta2), static_cast<double>(k)));
+    }
+    // scratch: [info 16 B, timeout flag 16 B][ab][bc]
+    const size_t ab_bytes = ab.size() * sizeof(unsigned long long);
+    const size_t bytes = 32 + ab_bytes + bc.size() * sizeof(float);
+    char* base = static_cast<char*>(scratch(bytes, 4));
+    if (!base) return fail(MRIP_ENOMEM, "mlp train: scratch allocation failed");
+    int* d_info = reinterpret_cast<int*>(base);
+    int* flag = reinterpret_cast<int*>(base + 16);
+    unsigned long long* d_ab = reinterpret_cast<unsigned long long*>(base + 32);
+    float* d_bc = reinterpret_cast<float*>(base + 32 + ab_bytes);
+    cudaError_t e = cudaMemsetAsync(base, 0, 32, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ab, ab.data(), ab_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_bc, bc.data(), bc.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_status(e, "mlp train: schedule upload");
+    const size_t smem = mlp_train_tc_smem(sp.d_in);
+    e = cudaFuncSetAttribute(mlp_train_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return cuda_status(e, "mlp train: shared memory attribute");
-    int* flag = nullptr;
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_tc_timeout);
-    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_status(e, "mlp train: timeout flag");
-    TrainArgs ta{X, Y, n_tr, B, (n_tr + B - 1) / B, epochs, d_in, d_ab, d_bc, lr, beta1, beta2, eps, theta,
-                 losses};
+    TrainArgs ta{sp.X, sp.Y, sp.n, sp.B, spe, sp.epochs, sp.d_in, d_ab, d_bc, sp.lr, sp.beta1, sp.beta2, sp.eps,
+                 sp.theta, sp.losses, sp.max_steps, sp.grad, sp.m_out, sp.v_out, sp.Xv, sp.Yv,
+                 sp.Xv ? sp.n_val : 0, sp.patience, sp.val_losses, d_info};
     mlp_train_tc_kernel<<<kTcCluster, kTcThreads, smem, st>>>(ta, flag);
     mrip_status s = launch_status("mlp train (tensor cores)");
     if (s != MRIP_OK) return s;
-    int h = 0;
-    e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int h[8] = {0};
+    e = cudaMemcpyAsync(h, base, 32, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // also: the host schedule dies at return
     if (e != cudaSuccess) return cuda_status(e, "mlp train (tensor cores)");
-    if (h) return fail(MRIP_ECUDA, "mlp train: a tensor-core MMA did not complete in time");
+    if (h[4]) return fail(MRIP_ECUDA, "mlp train: a tensor-core MMA did not complete in time");
+    if (info) {
+        info->epochs_run = h[0];
+        info->best_epoch = h[1];
+        info->steps = h[2];
+    }
     return MRIP_OK;
 }
 
@@ -950,6 +1080,54 @@ extern "C" mrip_status mrip_adam_step(float* d_theta, float* d_m, float* d_v, co
     adam_kernel<<<ceil_div_u(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_theta, d_m, d_v, d_grad, n,
                                                                                   lr, beta1, beta2, eps, bc1, bc2);
     return launch_status("mrip_adam_step");
+}
+
+extern "C" mrip_status mrip_mlp_train(int32_t d_in, const float* d_x, const float* d_y, int64_t n,
+                                      const float* d_xv, const float* d_yv, int64_t n_val,
+                                      const mrip_train_params* prm, float* d_theta, float* d_losses,
+                                      float* d_grad, float* d_m, float* d_v, float* d_val_losses,
+                                      int32_t* info_out, void* stream) {
+    if (d_in < 1 || d_in > kMaxIn || n < 1 || n_val < 0 || !prm)
+        return fail(MRIP_EINVAL, "mrip_mlp_train: d_in in 1..8, n >= 1, n_val >= 0, params");
+    if (prm->batch < 1 || prm->epochs < 1 || prm->patience < 0 || prm->max_steps < 0 || !(prm->lr > 0.0f) ||
+        !(prm->beta1 >= 0.0f && prm->beta1 < 1.0f) || !(prm->beta2 >= 0.0f && prm->beta2 < 1.0f) ||
+        !(prm->eps > 0.0f))
+        return fail(MRIP_EINVAL, "mrip_mlp_train: batch, epochs >= 1, patience, max_steps >= 0, lr, eps > 0, "
+                                 "beta1, beta2 in [0, 1)");
+    if (n > 0x7FFFFFFFll || n_val > 0x7FFFFFFFll) return fail(MRIP_EINVAL, "mrip_mlp_train: n, n_val < 2^31");
+    if (!d_x || !d_y || !d_theta || (n_val > 0 && (!d_xv || !d_yv)))
+        return fail(MRIP_EINVAL, "mrip_mlp_train: null pointer");
+    TrainSpec sp{};
+    sp.d_in = d_in;
+    sp.X = d_x;
+    sp.Y = d_y;
+    sp.n = n;
+    sp.Xv = n_val > 0 ? d_xv : nullptr;
+    sp.Yv = n_val > 0 ? d_yv : nullptr;
+    sp.n_val = n_val;
+    sp.B = prm->batch;
+    sp.epochs = prm->epochs;
+    sp.max_steps = prm->max_steps;
+    sp.patience = prm->patience;
+    sp.order_seed = prm->order_seed;
+    sp.lr = prm->lr;
+    sp.beta1 = prm->beta1;
+    sp.beta2 = prm->beta2;
+    sp.eps = prm->eps;
+    sp.theta = d_theta;
+    sp.losses = d_losses;
+    sp.grad = d_grad;
+    sp.m_out = d_m;
+    sp.v_out = d_v;
+    sp.val_losses = d_val_losses;
+    TrainInfo info{};
+    mrip_status s = mlp_train(sp, &info, static_cast<cudaStream_t>(stream));
+    if (s == MRIP_OK && info_out) {
+        info_out[0] = info.epochs_run;
+        info_out[1] = info.best_epoch;
+        info_out[2] = info.steps;
+    }
+    return s;
 }
 
 extern "C" mrip_status mrip_cv_reduce(const double* d_y, const double* d_g, int64_t n, const double* d_gc,

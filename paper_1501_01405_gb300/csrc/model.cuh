@@ -56,6 +56,10 @@ struct mrip_model {
     int64_t n_reps = 0;
     int64_t rep0 = 0;  // replication index of output column 0 (mrip_run_range)
     bool has_run = false;
+    // the network of the last mrip_run_cv
+    DevBuf cv_theta;
+    std::vector<double> cv_norm;
+    int cv_d_in = 0;
     // graph cache
     cudaGraphExec_t exec = nullptr;
     int32_t g_n_dp = -1;
@@ -90,7 +94,7 @@ mrip_status forest_fire_launch(const double* d_dps, int32_t n_dp, int64_t rep0, 
                                uint8_t* d_final, cudaStream_t st);
 mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t n_reps,
                         uint64_t seed, const mrip_cv_params* p, mrip_stat* plain_out,
-                        mrip_cv_stat* cv_out, float* loss_out);
+                        mrip_cv_stat* cv_out, mrip_cv_report* report);
 // network stages (mlp.cu)
 long long mlp_params(int d_in);
 mrip_status mlp_init(int d_in, uint64_t seed, float* theta, cudaStream_t st);
@@ -99,9 +103,33 @@ mrip_status mlp_step(const float* theta_in, int d_in, const float* X, long long 
                      const int64_t* idx, unsigned long long a, unsigned long long b, unsigned long long n_perm,
                      long long off, long long B, float* partial, float* grad, float* loss, float* theta,
                      float* m, float* v, const float* adam, cudaStream_t st);
-mrip_status mlp_train_tc(int d_in, const float* X, const float* Y, long long n_tr, long long B, int epochs,
-                         const unsigned long long* d_ab, const float* d_bc, float lr, float beta1, float beta2,
-                         float eps, float* theta, float* losses, cudaStream_t st);
+// One training run on the tensor cores (mlp.cu): inputs and outputs as
+// mrip_mlp_train.
+struct TrainSpec {
+    int d_in;
+    const float* X;   // d_in planes of n (standardised)
+    const float* Y;
+    long long n;
+    const float* Xv;  // validation, d_in planes of n_val (null: none)
+    const float* Yv;
+    long long n_val;
+    long long B;
+    int epochs;
+    long long max_steps;  // > 0: stop after this many steps
+    int patience;         // > 0: early stop on the validation loss
+    uint64_t order_seed;
+    float lr, beta1, beta2, eps;
+    float* theta;  // in: initial; out: trained (the kept epoch's)
+    float* losses;
+    float* grad;
+    float* m_out;
+    float* v_out;
+    float* val_losses;
+};
+struct TrainInfo {
+    int epochs_run, best_epoch, steps;
+};
+mrip_status mlp_train(const TrainSpec& spec, TrainInfo* info, cudaStream_t st);
 mrip_status mlp_forward(const float* theta, int d_in, const float* X, long long n, float* yhat,
                         cudaStream_t st);
 mrip_status cv_reduce(const double* y, const double* g, long long n, const double* gc, long long m,

@@ -8,8 +8,13 @@
 * one Adam step (FP32 vs FP64, 1e-5);
 * the per-design-point estimator on seeded arrays (FP64, 1e-12);
 * the whole mrip_run_cv pipeline against the oracle pipeline on small
-  tandem and forest-fire workloads: plain intervals 1e-12, training loss
-  within 5 %, control-variate means within their combined half-widths;
+  tandem and forest-fire workloads: plain intervals and standardisation
+  1e-12; given the GPU's trained network, the oracle's validation rho^2,
+  control-run count and intervals match (1e-2); the oracle's own training
+  reaches the same loss (5 %) and compatible means;
+* the gate: an informative early window keeps the control variate with
+  control runs sized from rho^2, an uninformative one declines it and
+  returns the plain intervals;
 * validity: coverage of the control-variate interval over 200 seeds;
 * what the network gains: on a workload whose early window is informative
   the control-variate half-width is smaller than the plain one computed on
@@ -134,26 +139,59 @@ def test_cv_reduce(env):
         assert o[d, 2] == pytest.approx(r["var"], rel=1e-11)
 
 
-def _compare_pipeline(plain, cv, loss, ref_plain, ref_cv, ref_loss):
+# the old pipeline semantics: no validation split, no gate, fixed control runs
+FIXED = dict(val_frac=0.0, patience=0, gate=False)
+
+
+def _compare_pipeline(m, kind, dps, n_reps, seed, model_kw, kw, threads):
+    """GPU pipeline vs the oracle pipeline.  (1) plain intervals 1e-12;
+    (2) the standardisation of the fit set 1e-12; (3) the rest of the
+    pipeline -- validation rho^2, control-run count, predictions, control
+    runs and estimator -- recomputed by the oracle from the GPU's trained
+    network: beta and the interval within 1e-2 (the GPU predicts in FP32 with
+    BF16 operands, so g differs from the FP64 oracle's by ~1e-3 relative);
+    (4) the oracle's own training for the epochs the GPU ran: last-epoch
+    loss within 5 %, means within the combined half-widths."""
+    plain, cv, rep = m.run_cv(dps, n_reps, seed, **kw)
+    theta, norm = m.cv_network()
+    ref_plain, ref_cv, info = ocv.run_cv(kind, dps, n_reps, seed, theta=theta.astype(np.float64),
+                                         threads=threads, **model_kw, **kw)
     for g, r in zip(plain, ref_plain):
         assert g["mean"] == pytest.approx(r["mean"], rel=1e-12)
         assert g["half_width"] == pytest.approx(r["half_width"], rel=1e-12)
-    assert loss == pytest.approx(ref_loss, rel=0.05)
-    for g, r in zip(cv, ref_cv):
-        assert g["n"] == r["n"] and g["m"] == r["m"]
-        assert abs(g["mean"] - r["mean"]) <= g["half_width"] + r["half_width"]
-        assert g["half_width"] == pytest.approx(r["half_width"], rel=0.25)
+    xm, xs, ym, ys = info["norm"]
+    np.testing.assert_allclose(norm[:-1, 0], xm, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(norm[:-1, 1], xs, rtol=1e-12)
+    assert norm[-1, 0] == pytest.approx(ym, rel=1e-12) and norm[-1, 1] == pytest.approx(ys, rel=1e-12)
+    if info["val_rho2"] is not None:
+        assert rep["val_rho2"] == pytest.approx(info["val_rho2"], abs=2e-3)
+    assert rep["declined"] == info["declined"]
+    assert rep["m_ctrl"] == info["m_ctrl"] or abs(rep["m_ctrl"] - info["m_ctrl"]) <= \
+        0.02 * info["m_ctrl"] + 1
+    if rep["m_ctrl"] == info["m_ctrl"]:
+        for g, r in zip(cv, ref_cv):
+            assert g["n"] == r["n"] and g["m"] == r["m"]
+            assert abs(g["mean"] - r["mean"]) <= 1e-2 * r["half_width"]
+            assert g["half_width"] == pytest.approx(r["half_width"], rel=1e-2)
+            assert g["beta"] == pytest.approx(r["beta"], rel=1e-2, abs=1e-3 * abs(r["beta"]) + 1e-12)
+    # the oracle trains for as many epochs as the GPU ran (with early stopping
+    # the two can stop at different epochs when validation losses nearly tie)
+    own_kw = dict(kw, epochs=rep["epochs_run"], patience=0)
+    _, own_cv, own = ocv.run_cv(kind, dps, n_reps, seed, threads=threads, **model_kw, **own_kw)
+    assert rep["train_loss"] == pytest.approx(own["loss"], rel=0.05)
+    if not rep["declined"] and not own["declined"]:
+        for g, r in zip(cv, own_cv):
+            assert abs(g["mean"] - r["mean"]) <= g["half_width"] + r["half_width"]
+    return plain, cv, rep
 
 
 def test_run_cv_tandem_matches_oracle_pipeline(env):
     eng, torch = env
     dps = mrip_inputs.tandem_design_points(8, seed=3)
-    kw = dict(train_frac=0.25, epochs=6, batch=64, lr=3e-3, m_ctrl=300)
+    kw = dict(train_frac=0.25, epochs=6, batch=64, lr=3e-3, m_ctrl=300, **FIXED)
     m = eng.Model(eng.MRIP_TANDEM3, n_clients=200, window=50)
-    plain, cv, loss = m.run_cv(dps, 48, 7, **kw)
-    ref_plain, ref_cv, ref_loss = ocv.run_cv("tandem3", dps, 48, 7, n_clients=200, window=50,
-                                             threads=oracle.host_threads(), **kw)
-    _compare_pipeline(plain, cv, loss, ref_plain, ref_cv, ref_loss)
+    _compare_pipeline(m, "tandem3", dps, 48, 7, dict(n_clients=200, window=50), kw,
+                      oracle.host_threads())
     m.close()
 
 
@@ -162,24 +200,69 @@ def test_run_cv_large_minibatch_matches_oracle_pipeline(env):
     of 128 samples per step (its gradient accumulates over both)."""
     eng, torch = env
     dps = mrip_inputs.tandem_design_points(16, seed=21)
-    kw = dict(train_frac=0.25, epochs=3, batch=2048, lr=3e-3, m_ctrl=60)
+    kw = dict(train_frac=0.25, epochs=3, batch=2048, lr=3e-3, m_ctrl=60, **FIXED)
     m = eng.Model(eng.MRIP_TANDEM3, n_clients=150, window=40)
-    plain, cv, loss = m.run_cv(dps, 600, 9, **kw)
-    ref_plain, ref_cv, ref_loss = ocv.run_cv("tandem3", dps, 600, 9, n_clients=150, window=40,
-                                             threads=oracle.host_threads(), **kw)
-    _compare_pipeline(plain, cv, loss, ref_plain, ref_cv, ref_loss)
+    _compare_pipeline(m, "tandem3", dps, 600, 9, dict(n_clients=150, window=40), kw,
+                      oracle.host_threads())
     m.close()
 
 
 def test_run_cv_forest_fire_matches_oracle_pipeline(env):
     eng, torch = env
     dps = mrip_inputs.ff_cv_design_points(4)
-    kw = dict(train_frac=0.25, epochs=8, batch=32, lr=3e-3, m_ctrl=40)
+    kw = dict(train_frac=0.25, epochs=8, batch=32, lr=3e-3, m_ctrl=40, **FIXED)
     m = eng.Model(eng.MRIP_FOREST_FIRE, L=32, n_steps=200, density=0.5, window=40)
-    plain, cv, loss = m.run_cv(dps, 24, 5, **kw)
-    ref_plain, ref_cv, ref_loss = ocv.run_cv("forest_fire", dps, 24, 5, L=32, n_steps=200,
-                                             window=40, threads=oracle.host_threads(), **kw)
-    _compare_pipeline(plain, cv, loss, ref_plain, ref_cv, ref_loss)
+    _compare_pipeline(m, "forest_fire", dps, 24, 5, dict(L=32, n_steps=200, window=40), kw,
+                      oracle.host_threads())
+    m.close()
+
+
+def test_run_cv_validation_gate_accepts_informative_window(env):
+    """120 clients with a 100-client window: the early window explains about
+    half of each replication's within-design-point variance (linear R^2
+    0.55 by the oracle), well above the break-even rho^2 of 1 - n_held /
+    (1.1 n_reps) = 0.27 when a fifth of the replications train the network;
+    the control variate is kept, its control runs are sized from the
+    validation rho^2 (m_ctrl = 0), and the oracle, given the GPU's network,
+    finds the same rho^2 and count."""
+    eng, torch = env
+    dps = mrip_inputs.tandem_design_points(12, seed=5)
+    kw = dict(train_frac=0.2, val_frac=0.25, epochs=40, patience=5, batch=64, lr=3e-3,
+              m_ctrl=0, gate=True)
+    m = eng.Model(eng.MRIP_TANDEM3, n_clients=120, window=100)
+    plain, cv, rep = _compare_pipeline(m, "tandem3", dps, 160, 3,
+                                       dict(n_clients=120, window=100), kw,
+                                       oracle.host_threads())
+    assert not rep["declined"] and rep["var_ratio"] < 1.0, rep
+    assert rep["n_val"] == math.ceil(0.25 * math.ceil(0.2 * 160))
+    assert rep["m_ctrl"] == ocv.control_runs(rep["val_rho2"], 160 - math.ceil(0.2 * 160))
+    assert 1 <= rep["best_epoch"] <= rep["epochs_run"] <= 40
+    assert np.isfinite(rep["val_loss"])
+    for k in ("ms_simulate", "ms_train", "ms_control", "ms_infer", "ms_estimate"):
+        assert rep[k] > 0.0, k
+    m.close()
+
+
+def test_run_cv_gate_declines_uninformative_window(env):
+    """2,000 clients and a 10-client window: the early window says almost
+    nothing about the replication mean, so the predicted variance ratio is
+    >= 1 and the plain intervals are returned as the control-variate
+    result, with no control runs."""
+    eng, torch = env
+    dps = mrip_inputs.tandem_design_points(64, seed=6)
+    kw = dict(train_frac=0.1, val_frac=0.2, epochs=10, patience=2, batch=256, lr=1e-3,
+              m_ctrl=0, gate=True)
+    m = eng.Model(eng.MRIP_TANDEM3, n_clients=2000, window=10)
+    plain, cv, rep = m.run_cv(dps, 100, 8, **kw)
+    assert rep["declined"] and rep["m_ctrl"] == 0 and rep["var_ratio"] >= 1.0
+    for p, c in zip(plain, cv):
+        assert c["mean"] == p["mean"] and c["half_width"] == p["half_width"] and c["m"] == 0
+    assert rep["ms_control"] == 0.0 and rep["ms_infer"] == 0.0
+    theta, _ = m.cv_network()
+    _, _, info = ocv.run_cv("tandem3", dps, 100, 8, n_clients=2000, window=10,
+                            theta=theta.astype(np.float64), threads=oracle.host_threads(), **kw)
+    assert info["declined"]
+    assert rep["val_rho2"] == pytest.approx(info["val_rho2"], abs=2e-3)
     m.close()
 
 
@@ -195,7 +278,7 @@ def test_cv_interval_coverage(env):
     trials = 200
     for k in range(trials):
         _, cv, _ = m.run_cv(dps, 64, 10_000 + k, train_frac=0.25, epochs=3, batch=32, lr=3e-3,
-                            m_ctrl=640)
+                            m_ctrl=640, **FIXED)
         for d in range(2):
             hits[d] += abs(cv[d]["mean"] - truth[d]) <= cv[d]["half_width"]
     rate = hits.sum() / (2 * trials)
@@ -211,8 +294,8 @@ def test_network_gain_when_the_window_is_informative(env):
     eng, torch = env
     dps = mrip_inputs.tandem_design_points(16, seed=5)
     m = eng.Model(eng.MRIP_TANDEM3, n_clients=150, window=75)
-    plain, cv, loss = m.run_cv(dps, 256, 3, train_frac=0.25, epochs=40, batch=256, lr=3e-3,
-                               m_ctrl=2000)
+    plain, cv, rep = m.run_cv(dps, 256, 3, train_frac=0.25, epochs=40, batch=256, lr=3e-3,
+                              m_ctrl=2000, **FIXED)
     n_held = cv[0]["n"]
     Y = m.outputs(0).reshape(16, 256)[:, 256 - n_held:]
     ratios = [c["half_width"] / ostats.ci(Y[d])["half_width"] for d, c in enumerate(cv)]

@@ -197,7 +197,7 @@ def test_training_learns_a_smooth_function():
     rng = np.random.default_rng(5)
     X = rng.uniform(-1, 1, size=(2048, 8))
     y = 2.0 * X[:, 0] - X[:, 1] + 0.5 * X[:, 2] ** 2 + 3.0
-    theta, norm, losses = omlp.train(X, y, 8, 42, epochs=15, batch=256, lr=3e-3)
+    theta, norm, losses, _ = omlp.train(X, y, 8, 42, epochs=15, batch=256, lr=3e-3)
     assert losses[-1] < 0.05 * losses[0]
     pred = omlp.predict(theta, X, norm, 8) * norm[3] + norm[2]
     assert np.sqrt(np.mean((pred - y) ** 2)) < 0.2 * y.std()
@@ -241,3 +241,90 @@ def test_cv_coverage_and_variance_reduction():
     # half-width ratio -> sqrt(1 - rho^2 + rho^2 n / M)
     expect = math.sqrt(1 - rho**2 + rho**2 * n / M)
     assert np.median(ratio) == pytest.approx(expect, rel=0.1)
+
+
+def test_training_early_stop_rule():
+    """With a validation set the kept parameters are those after the epoch of
+    lowest validation loss -- the same as a run stopped there -- and training
+    ends `patience` epochs later; the validation loss is the mean squared
+    error of the standardised target, computed independently here."""
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-1, 1, size=(600, 6))
+    y = np.sin(3 * X[:, 0]) + X[:, 1] * X[:, 2]
+    Xv = rng.uniform(-1, 1, size=(200, 6))
+    yv = -(np.sin(3 * Xv[:, 0]) + Xv[:, 1] * Xv[:, 2])  # anti-correlated target
+    theta, norm, losses, info = omlp.train(X, y, 6, 11, epochs=12, batch=128, lr=3e-3,
+                                           X_val=Xv, y_val=yv, patience=2)
+    vl, best, run = info["val_losses"], info["best_epoch"], info["epochs_run"]
+    assert len(vl) == run and len(losses) == run * 5
+    assert best == int(np.argmin(vl)) + 1 and run == best + 2 and run < 12
+    assert all(vl[k] >= vl[best - 1] for k in range(best, run))
+    ref, _, _, _ = omlp.train(X, y, 6, 11, epochs=best, batch=128, lr=3e-3)
+    assert np.array_equal(theta, ref)
+    pred = omlp.predict(theta, Xv, norm, 6)
+    ystd = (yv - norm[2]) / norm[3]
+    assert vl[best - 1] == pytest.approx(np.mean((pred - ystd) ** 2), rel=1e-6)
+
+
+def test_within_rho2_known_correlation_and_offsets():
+    """Pooled within-design-point rho^2: design-point offsets do not enter;
+    an exact affine control gives 1, an independent one about 0, and a
+    bivariate normal with correlation rho about rho^2."""
+    rng = np.random.default_rng(4)
+    n_dp, n = 400, 6
+    y = rng.standard_normal((n_dp, n))
+    g = 0.6 * y + 0.8 * rng.standard_normal((n_dp, n))
+    off_y = rng.uniform(-50, 50, size=(n_dp, 1))
+    off_g = rng.uniform(-50, 50, size=(n_dp, 1))
+    r = ocv.within_rho2(y, g)
+    assert r == pytest.approx(ocv.within_rho2(y + off_y, g + off_g), rel=1e-9)
+    # sampling error of a pooled correlation on 400 x 5 degrees of freedom
+    assert abs(math.sqrt(r) - 0.6) < 4 * (1 - 0.36) / math.sqrt(n_dp * (n - 1))
+    assert ocv.within_rho2(y, -2.0 * y + off_g) == pytest.approx(1.0, rel=1e-12)
+    assert ocv.within_rho2(y, rng.standard_normal((n_dp, n))) < 0.01
+    # a single replication per design point carries no within information
+    assert ocv.within_rho2(y[:, :1], g[:, :1]) == 0.0
+
+
+def test_within_rho2_equal_weights_with_fit_scales():
+    """Design points of very different variance: half have a correlated
+    control (rho 0.9) and a scale 100 times the others', half an
+    uncorrelated one.  Unscaled pooling is dominated by the large ones
+    (rho^2 ~ 0.81); scaled by each design point's fit-set deviations every
+    design point weighs the same and the estimate is the squared mean
+    correlation, (0.9 / 2)^2 ~ 0.2."""
+    rng = np.random.default_rng(12)
+    n_dp, n_val, n_fit = 600, 4, 40
+
+    def draw(n):
+        z1 = rng.standard_normal((n_dp, n))
+        z2 = rng.standard_normal((n_dp, n))
+        rho = np.where(np.arange(n_dp) % 2 == 0, 0.9, 0.0)[:, None]
+        scale = np.where(np.arange(n_dp) % 2 == 0, 100.0, 1.0)[:, None]
+        return scale * z1, scale * (rho * z1 + np.sqrt(1 - rho**2) * z2)
+    yv, gv = draw(n_val)
+    yf, gf = draw(n_fit)
+    assert ocv.within_rho2(yv, gv) == pytest.approx(0.81, abs=0.05)
+    assert ocv.within_rho2(yv, gv, yf, gf) == pytest.approx(0.45**2, abs=0.05)
+    # a constant fit output leaves its design point out
+    gf0 = gf.copy()
+    gf0[1::2] = 3.0
+    assert ocv.within_rho2(yv, gv, yf, gf0) == pytest.approx(0.81, abs=0.05)
+
+
+def test_control_run_sizing_and_gate():
+    # M keeps beta^2 Var(g')/M <= 0.1 (1 - rho^2) s^2 / n: closed values
+    assert ocv.control_runs(None, 230) == 2300
+    assert ocv.control_runs(0.0, 230) == 2
+    assert ocv.control_runs(0.5, 230) == 2300
+    assert ocv.control_runs(0.02, 230) == math.ceil(230 * 0.02 / (0.1 * 0.98))
+    assert ocv.control_runs(0.9999999, 230) == 23000
+    for rho2 in (0.05, 0.3, 0.8):
+        M = ocv.control_runs(rho2, 230)
+        assert rho2 / M <= 0.1 * (1 - rho2) / 230 * (1 + 1e-12)
+    # the gate: no correlation -> training replications are pure loss
+    assert ocv.var_ratio(0.0, 256, 230, 2) == pytest.approx(256 / 230)
+    # break-even rho^2 with M sized as above: (1 + 0.1) (1 - rho^2) n_reps / n_held = 1
+    rho_be = 1 - 230 / (256 * 1.1)
+    assert ocv.var_ratio(rho_be + 0.01, 256, 230, ocv.control_runs(rho_be + 0.01, 230)) < 1.0
+    assert ocv.var_ratio(rho_be - 0.01, 256, 230, ocv.control_runs(rho_be - 0.01, 230)) > 1.0
