@@ -35,16 +35,28 @@ inline RoundKeys expand_key(uint64_t seed) {
     return rk;
 }
 
+// The full 64-bit product of two 32-bit words as one widening multiply
+// (mul.wide.u32), both halves from one instruction.
+__host__ __device__ __forceinline__ void mul_wide_u32(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+#ifdef __CUDA_ARCH__
+    unsigned long long r;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(b));
+#else
+    const uint64_t r = static_cast<uint64_t>(a) * b;
+#endif
+    hi = static_cast<uint32_t>(r >> 32);
+    lo = static_cast<uint32_t>(r);
+}
+
 // One Philox4x32 round: products of (0xD2511F53, x0) and (0xCD9E8D57, x2);
 // high halves xored with the other words and the round key; low halves
 // moved to positions 1 and 3.
 __host__ __device__ __forceinline__ void philox_round(uint32_t& x0, uint32_t& x1, uint32_t& x2,
                                                       uint32_t& x3, uint32_t ka, uint32_t kb) {
 #ifdef __CUDA_ARCH__
-    const uint32_t p0_lo = 0xD2511F53u * x0;
-    const uint32_t p0_hi = __umulhi(0xD2511F53u, x0);
-    const uint32_t p1_lo = 0xCD9E8D57u * x2;
-    const uint32_t p1_hi = __umulhi(0xCD9E8D57u, x2);
+    uint32_t p0_lo, p0_hi, p1_lo, p1_hi;
+    mul_wide_u32(0xD2511F53u, x0, p0_hi, p0_lo);
+    mul_wide_u32(0xCD9E8D57u, x2, p1_hi, p1_lo);
 #else
     const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * x0;
     const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * x2;

@@ -44,11 +44,10 @@ struct StepKey {
 
 __device__ __forceinline__ StepKey step_key(uint32_t t, uint32_t rep, const RoundKeys& rk) {
     StepKey s;
-    const uint32_t h1 = __umulhi(0xCD9E8D57u, rep);
+    uint32_t h1;
+    mul_wide_u32(0xCD9E8D57u, rep, h1, s.x1);
     s.x0 = h1 ^ t ^ rk.k0[0];
-    s.x1 = 0xCD9E8D57u * rep;
-    s.p_hi = __umulhi(0xD2511F53u, s.x0);
-    s.p_lo = 0xD2511F53u * s.x0;
+    mul_wide_u32(0xD2511F53u, s.x0, s.p_hi, s.p_lo);
     return s;
 }
 
@@ -62,8 +61,8 @@ __device__ __forceinline__ uint4 philox_step(unsigned long long prod, uint32_t c
     const uint32_t a_lo = static_cast<uint32_t>(prod);
     const uint32_t w2 = a_hi ^ c3 ^ rk.k1[0];
     // round 2: the product with word 0 is sk.p
-    const uint32_t b_hi = __umulhi(0xCD9E8D57u, w2);
-    const uint32_t b_lo = 0xCD9E8D57u * w2;
+    uint32_t b_hi, b_lo;
+    mul_wide_u32(0xCD9E8D57u, w2, b_hi, b_lo);
     uint32_t x0 = b_hi ^ sk.x1 ^ rk.k0[1];
     uint32_t x1 = b_lo;
     uint32_t x2 = sk.p_hi ^ a_lo ^ rk.k1[1];

@@ -398,11 +398,13 @@ struct TrainArgs {
 //   Z2  = H1~ W2~^T       (K 64)
 //   dH1 = dZ2~ W2~        (K 64, B = W2~ transposed)
 //   dW2 = dZ2~^T H1~      (M 128 with rows 64..127 zero, K = the 128 samples)
+//   dW1 = dZ1~^T X~       (M 128 with rows 64..127 zero, N 16, K = the 128 samples)
 // Each thread turns its 16 columns of a row of Z1 / Z2 / dH1 into
 // activations, residual and deltas (FP32, rounded to BF16 where the next
 // contraction reads them) and writes them in the operands' core-matrix
-// layouts; the bias, W3 and W1 gradients are FP32 column sums over the tile
-// in a fixed order (chunks of 16 samples, then the chunks in order).  After a cluster barrier CTA r owns the r-th slice of the
+// layouts (16-byte stores where a row's 8 columns are contiguous); the bias
+// and W3 gradients are FP32 column sums over the tile in a fixed order
+// (chunks of 16 samples, then the chunks in order).  After a cluster barrier CTA r owns the r-th slice of the
 // parameters: it adds that slice of every CTA's gradient in rank order over
 // distributed shared memory, applies Adam and writes the new values into
 // every CTA's copy; a second barrier ends the step.  Same arithmetic as
@@ -425,10 +427,10 @@ struct TcSmem {
     alignas(1024) unsigned char w2tb[H * H * 2];           // W2~ [u][v] as B
     alignas(1024) unsigned char h1tt[H * kTcRows * 2];     // H1~ transposed [u][m], K = 128
     alignas(1024) unsigned char a3[kTcRows * H * 2];       // dZ2~ rows, K = 64
-    alignas(1024) unsigned char dz2tt[kTcRows * kTcRows * 2];  // dZ2~ transposed [v][m]; rows 64.. zero
+    alignas(1024) unsigned char dz2tt[kTcRows * kTcRows * 2];  // dZ2~, then dZ1~, transposed [v][m]; rows 64.. zero
+    alignas(1024) unsigned char xtt[16 * kTcRows * 2];     // X~ transposed [k][m], K = 128; rows d_in.. zero
     float f32[kTcRows][H + 1];                             // dZ2, then dZ1 (FP32)
     __nv_bfloat16 h2t[kTcRows][H + 2];                     // H2~ rows (for dW3)
-    float xs[kTcRows][kMaxIn + 1];                         // X~ (for dW1)
     float ypart[4][kTcRows];                               // output partials per column block
     float colpart[3][kTcChunks][H];                        // column sums per row chunk
     float dy[kTcRows], r2[kTcRows];
@@ -440,6 +442,18 @@ struct TcSmem {
 
 __device__ __forceinline__ void put_bf16(unsigned char* tile, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(tile + off) = __float2bfloat16_rn(v);
+}
+
+// Eight FP32 values rounded to BF16 (nearest even), the first at the lowest
+// address: one core-matrix row of 16 bytes.
+__device__ __forceinline__ uint4 pack_bf16x8(const float* w) {
+    uint32_t r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(w[2 * q], w[2 * q + 1]);
+        r[q] = *reinterpret_cast<const uint32_t*>(&p);
+    }
+    return make_uint4(r[0], r[1], r[2], r[3]);
 }
 
 __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads, 1)
@@ -463,6 +477,7 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     const int c0 = 16 * cb;                         // its 16 columns
     const int p_lo = rank * slice, p_hi = min(P, p_lo + slice);
     constexpr uint32_t kIdesc = tc::idesc_bf16(kTcRows, H);
+    constexpr uint32_t kIdescW1 = tc::idesc_bf16(kTcRows, 16);
 
     if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
     if (t == 0) tc::mbar_init(&S.bar);
@@ -473,8 +488,10 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     }
     for (int i = t; i < kTcRows * kTcRows * 2 / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(S.dz2tt)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = t; i < kTcRows * 16 * 2 / 16; i += kTcThreads)
+    for (int i = t; i < kTcRows * 16 * 2 / 16; i += kTcThreads) {
         reinterpret_cast<uint4*>(S.a1)[i] = make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<uint4*>(S.xtt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     tc::fence_before_sync();
     cluster.sync();
     tc::fence_after_sync();
@@ -501,17 +518,30 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
         __syncthreads();
         tc::fence_after_sync();
     };
-    // BF16 operands (and FP32 biases) of the current parameters th
+    // BF16 operands (and FP32 biases) of the current parameters th; every
+    // thread packs 8 consecutive K elements of one operand row into one
+    // 16-byte store (a core-matrix row)
     auto stage_weights = [&]() {
-        for (int i = t; i < H * 16; i += kTcThreads) {
-            const int u = i >> 4, k = i & 15;
-            put_bf16(S.w1b, tc::core_offset(u, k, 16), k < d_in ? theta_w1(th, d_in, u, k) : 0.0f);
+        if (t < 2 * H) {  // W1~ as B: row u, K = the 16 (zero-padded) inputs
+            const int u = t >> 1, k0 = 8 * (t & 1);
+            float w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] = k0 + q < d_in ? theta_w1(th, d_in, u, k0 + q) : 0.0f;
+            *reinterpret_cast<uint4*>(S.w1b + tc::core_offset(u, k0, 16)) = pack_bf16x8(w);
         }
-        for (int i = t; i < H * H; i += kTcThreads) {
-            const int v = i / H, u = i - v * H;
-            const float w = th[off_w2(d_in) + i];
-            put_bf16(S.w2b, tc::core_offset(v, u, H), w);
-            put_bf16(S.w2tb, tc::core_offset(u, v, H), w);
+        {   // W2~ [v][u] as B of Z2 (K = u): row v, columns 8j .. 8j + 7
+            const int v = t >> 3, j = t & 7;
+            const float4* src = reinterpret_cast<const float4*>(th + off_w2(d_in) + v * H + 8 * j);
+            const float4 a = src[0], b = src[1];
+            const float w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            *reinterpret_cast<uint4*>(S.w2b + tc::core_offset(v, 8 * j, H)) = pack_bf16x8(w);
+        }
+        {   // W2~ transposed [u][v] as B of dH1 (K = v): row u, columns 8j .. 8j + 7
+            const int u = t & (H - 1), j = t >> 6;
+            float w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] = th[off_w2(d_in) + (8 * j + q) * H + u];
+            *reinterpret_cast<uint4*>(S.w2tb + tc::core_offset(u, 8 * j, H)) = pack_bf16x8(w);
         }
         for (int i = t; i < H; i += kTcThreads) {
             S.w3[i] = bf(th[off_w3(d_in) + i]);
@@ -526,10 +556,10 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     // columns in mask1 / mask2; returns the output of row m without b3.
     auto forward_tile = [&](const float* Xs, long long n_total, long long smp, bool valid, uint32_t& mask1,
                             uint32_t& mask2) -> float {
-        for (int k = 2 * cb; k < 2 * cb + 2; ++k) {  // features 2cb, 2cb + 1 of row m
-            const float x = (valid && k < d_in) ? bf(Xs[k * n_total + smp]) : 0.0f;
-            S.xs[m][k] = x;
-            if (k < d_in) put_bf16(S.a1, tc::core_offset(m, k, 16), x);
+        for (int k = 2 * cb; k < 2 * cb + 2 && k < d_in; ++k) {  // features 2cb, 2cb + 1 of row m
+            const float x = valid ? bf(Xs[k * n_total + smp]) : 0.0f;
+            put_bf16(S.a1, tc::core_offset(m, k, 16), x);
+            put_bf16(S.xtt, tc::core_offset(k, m, kTcRows), x);
         }
         sync_for_mma();
         if (t == 0 && ok) {
@@ -548,10 +578,11 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
                 const int u = c0 + j;
                 const float h = fmaxf(z[j] + S.b1[u], 0.0f);
                 if (h > 0.0f) mask1 |= 1u << j;
-                const float hb = bf(h);
-                put_bf16(S.a2, tc::core_offset(m, u, H), hb);
-                put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), hb);
+                z[j] = bf(h);
+                put_bf16(S.h1tt, tc::core_offset(u, m, kTcRows), z[j]);
             }
+            *reinterpret_cast<uint4*>(S.a2 + tc::core_offset(m, c0, H)) = pack_bf16x8(z);
+            *reinterpret_cast<uint4*>(S.a2 + tc::core_offset(m, c0 + 8, H)) = pack_bf16x8(z + 8);
         }
         sync_for_mma();
         if (t == 0 && ok) {
@@ -614,14 +645,18 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
                     S.dy[m] = dyv;
                     S.r2[m] = r * r;
                 }
+                {
+                    float db[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int v = c0 + j;
-                    const float d = ((mask2 >> j) & 1u) ? dyv * S.w3[v] : 0.0f;
-                    S.f32[m][v] = d;
-                    const float db = bf(d);
-                    put_bf16(S.a3, tc::core_offset(m, v, H), db);
-                    put_bf16(S.dz2tt, tc::core_offset(v, m, kTcRows), db);
+                    for (int j = 0; j < 16; ++j) {
+                        const int v = c0 + j;
+                        const float d = ((mask2 >> j) & 1u) ? dyv * S.w3[v] : 0.0f;
+                        S.f32[m][v] = d;
+                        db[j] = bf(d);
+                        put_bf16(S.dz2tt, tc::core_offset(v, m, kTcRows), db[j]);
+                    }
+                    *reinterpret_cast<uint4*>(S.a3 + tc::core_offset(m, c0, H)) = pack_bf16x8(db);
+                    *reinterpret_cast<uint4*>(S.a3 + tc::core_offset(m, c0 + 8, H)) = pack_bf16x8(db + 8);
                 }
                 sync_for_mma();
                 if (t == 0 && ok) {
@@ -664,12 +699,18 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
                     part[off_b3(d_in)] += a;
                     part[P] += l;
                 }
-                // dZ1 = dH1 [z1 > 0]; dW2 rows 0..63 (TMEM lanes 0..63) into the gradient
+                // dZ1 = dH1 [z1 > 0] (FP32 for b1; BF16 transposed into the
+                // freed dZ2~ buffer for dW1); dW2 rows 0..63 (TMEM lanes 0..63)
+                // into the gradient
                 {
                     float z[16];
                     tc::tmem_ld16(tm + lane_base + c0, z);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) S.f32[m][c0 + j] = ((mask1 >> j) & 1u) ? z[j] : 0.0f;
+                    for (int j = 0; j < 16; ++j) {
+                        const float d = ((mask1 >> j) & 1u) ? z[j] : 0.0f;
+                        S.f32[m][c0 + j] = d;
+                        put_bf16(S.dz2tt, tc::core_offset(c0 + j, m, kTcRows), d);
+                    }
                 }
                 if (quarter < 2) {
                     float z[16];
@@ -677,29 +718,35 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
 #pragma unroll
                     for (int j = 0; j < 16; ++j) part[off_w2(d_in) + m * H + c0 + j] += z[j];
                 }
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                // column sums of dZ1: b1 per chunk, W1 with BF16-rounded dZ1 (one output per thread)
+                sync_for_mma();
+                if (t == 0 && ok) {
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks)  // dW1 = dZ1~^T X~
+                        tc::mma_bf16(tm + 192, tc::smem_desc(tc::smem_addr(S.dz2tt) + 256 * ks, 128, 2048),
+                                     tc::smem_desc(tc::smem_addr(S.xtt) + 256 * ks, 128, 2048), kIdescW1, ks > 0);
+                    tc::mma_commit(&S.bar);
+                }
+                // meanwhile: column sums of dZ1 (b1) per chunk
                 {
                     const int u = t & (H - 1), ch = t / H;
                     float a1 = 0.0f;
                     for (int q = 16 * ch; q < 16 * ch + 16; ++q) a1 += S.f32[q][u];
                     S.colpart[2][ch][u] = a1;
                 }
-                if (t < H * d_in) {
-                    const int u = t / d_in, k = t - u * d_in;
-                    float acc = 0.0f;
-                    for (int q = 0; q < kTcRows; ++q) acc = fmaf(bf(S.f32[q][u]), S.xs[q][k], acc);
-                    part[t] += acc;
-                }
-                __syncthreads();
+                wait_mma();
                 if (t < H) {
                     float a1 = 0.0f;
                     for (int ch = 0; ch < kTcChunks; ++ch) a1 += S.colpart[2][ch][t];
                     part[off_b1(d_in) + t] += a1;
                 }
+                if (quarter < 2 && cb == 0) {  // dW1 rows u = m < 64 (TMEM lanes 0..63), columns = inputs
+                    float z[16];
+                    tc::tmem_ld16(tm + lane_base + 192, z);
+                    for (int k = 0; k < d_in; ++k) part[m * d_in + k] += z[k];
+                }
+                tc::fence_before_sync();
                 __syncthreads();
+                tc::fence_after_sync();
             }
             cluster.sync();  // every CTA's gradient is complete
             const float bc1 = ta.bc[2 * step], bc2 = ta.bc[2 * step + 1];
