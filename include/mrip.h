@@ -221,10 +221,15 @@ mrip_status mrip_autotune(mrip_model *model, const double *design_points, int32_
  *      M = ceil(n_held rho^2 / (0.1 (1 - rho^2))), clamped to
  *      [2, 100 n_held], so that the control mean adds at most a tenth to
  *      the residual variance (10 n_held without validation);
- *   4. gate != 0: predicts the variance ratio of the control-variate and
- *      plain estimators at this n, n_reps ((1 - rho^2) / n_held + rho^2 / M),
- *      and when it is >= 1 declines: cv_out gets the plain intervals
- *      (m = 0, beta = 0) and report->declined = 1;
+ *   4. gate != 0: after the first ceil(64 / steps per epoch) epochs (at
+ *      least 64 Adam steps; only if that is fewer than `epochs`), a
+ *      validation rho^2 below a quarter of the break-even
+ *      1 - n_held / (1.1 n_reps) declines at once (report->declined = 2, no
+ *      further training; the run otherwise resumes exactly); after training,
+ *      predicts the variance ratio of the control-variate and plain
+ *      estimators at this n, n_reps ((1 - rho^2) / n_held + rho^2 / M),
+ *      and when it is >= 1 declines (report->declined = 1).  Declined:
+ *      cv_out gets the plain intervals (m = 0, beta = 0);
  *   5. otherwise predicts g for the n_held = n_reps - n_train held-out
  *      replications and for the M control runs -- the replications
  *      n_reps .. n_reps + M - 1 of the same streams (tag 0), simulated for
@@ -251,7 +256,8 @@ typedef struct {
 } mrip_cv_params;
 
 typedef struct {
-    int32_t declined;    /* 1: cv_out holds the plain intervals                 */
+    int32_t declined;    /* 0 kept; 1 declined after training, 2 by the screen   */
+                         /* after the first epochs: cv_out = plain intervals   */
     int32_t epochs_run;
     int32_t best_epoch;  /* the epoch whose parameters were kept (1-based)      */
     int32_t n_val;       /* validation replications per design point            */
@@ -503,6 +509,9 @@ mrip_status mrip_mlp_loss_grad(const float *d_theta, int32_t d_in, const float *
  *   d_xv, d_yv    the validation set, d_in planes of n_val, and n_val
  *   d_theta       in: initial parameters (mrip_mlp_param_count floats);
  *                 out: the trained ones (the kept epoch's with validation)
+ *   d_m_in, d_v_in  Adam's moments to resume from (may be NULL: zero) --
+ *                 with params->epoch0 = e this continues a run stopped after
+ *                 e epochs: epoch order and Adam's step count go on from there
  *   d_losses      per Adam step (may be NULL; room for every step run)
  *   d_grad        the gradient of the last step (may be NULL)
  *   d_m, d_v      Adam's moments after the last step (may be NULL)
@@ -513,15 +522,18 @@ mrip_status mrip_mlp_loss_grad(const float *d_theta, int32_t d_in, const float *
  * complete within its wait limit returns MRIP_ECUDA. */
 typedef struct {
     int64_t batch;        /* minibatch size >= 1                              */
-    int32_t epochs;       /* >= 1                                             */
+    int32_t epochs;       /* >= 1 (epochs of this call)                       */
     int32_t patience;     /* >= 0; early stop on the validation loss          */
     int64_t max_steps;    /* > 0: stop after this many Adam steps; 0: none    */
     float lr, beta1, beta2, eps;
     uint64_t order_seed;  /* minibatch order (stream tag 4)                   */
+    int32_t epoch0;       /* >= 0: index of this call's first epoch (resume)  */
+    int32_t pad;
 } mrip_train_params;
 mrip_status mrip_mlp_train(int32_t d_in, const float *d_x, const float *d_y, int64_t n,
                            const float *d_xv, const float *d_yv, int64_t n_val,
-                           const mrip_train_params *params, float *d_theta, float *d_losses,
+                           const mrip_train_params *params, float *d_theta,
+                           const float *d_m_in, const float *d_v_in, float *d_losses,
                            float *d_grad, float *d_m, float *d_v, float *d_val_losses,
                            int32_t *info_out, void *stream);
 

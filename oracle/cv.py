@@ -26,7 +26,10 @@ leaves a residual variance (1 - rho^2) s^2 and the control mean adds about
 rho^2 s^2 / M, so M = ceil(n rho^2 / (0.1 (1 - rho^2))) keeps that term to a
 tenth of the residual one, and the control-variate estimator beats the
 plain one on all n_reps replications only if
-n_reps ((1 - rho^2) / n + rho^2 / M) < 1.
+n_reps ((1 - rho^2) / n + rho^2 / M) < 1, i.e. (M sized so) rho^2 above
+about 1 - n / (1.1 n_reps).  A network trained for the first
+ceil(64 / steps per epoch) epochs whose validation rho^2 is below a quarter
+of that declines without further training.
 """
 import math
 
@@ -138,7 +141,10 @@ def run_cv(kind, dps, n_reps, seed, n_clients=None, window=100, L=None, n_steps=
     set (design-point-major order) with early stopping on the validation set
     -- or, with `theta` given, take that network; estimate the pooled
     within-design-point rho^2 on the validation set; size the control runs
-    (m_ctrl None or 0: control_runs); with `gate`, decline when the
+    (m_ctrl None or 0: control_runs); with `gate`, decline right after
+    the first ceil(64 / steps per epoch) epochs when the validation rho^2
+    is below a quarter of the break-even 1 - n_held / (1.1 n_reps) (the
+    screen), and after training when the
     predicted variance ratio is >= 1 (cv = the plain intervals); else
     predict held-out and control runs and estimate per design point.
     Returns (plain intervals, cv dicts, info dict)."""
@@ -169,10 +175,30 @@ def run_cv(kind, dps, n_reps, seed, n_clients=None, window=100, L=None, n_steps=
     yfit = Y[:, :n_fit].reshape(-1)
     Xval = F[:, n_fit:n_train].reshape(-1, d_in)
     yval = Y[:, n_fit:n_train].reshape(-1)
+    def val_rho2(th, nrm):
+        g_val = _mlp.f32(_mlp.predict(th, Xval, nrm, d_in)).reshape(n_dp, n_val)
+        g_fit = _mlp.f32(_mlp.predict(th, Xfit, nrm, d_in)).reshape(n_dp, n_fit)
+        return within_rho2(Y[:, n_fit:n_train], g_val, Y[:, :n_fit], g_fit)
+
+    # the screen: after the first ceil(64 / steps per epoch) epochs (at least
+    # 64 Adam steps), a validation rho^2 below a quarter of the break-even
+    # value 1 - n_held / (1.1 n_reps) declines at once
+    rho2_be = 1.0 - n_held / (1.1 * n_reps)
+    screen = {"rho2": None}
+    spe = -(-Xfit.shape[0] // batch)
+    screen_epochs = min(epochs, -(-64 // spe))
+
+    def after_epoch(e, th, nrm):
+        if e != screen_epochs or not gate or screen_epochs >= epochs or n_val < 2:
+            return False
+        screen["rho2"] = val_rho2(th, nrm)
+        return screen["rho2"] < 0.25 * rho2_be
+
     if theta is None:
         theta, norm, losses, tinfo = _mlp.train(Xfit, yfit, d_in, net_seed, epochs, batch=batch,
                                                 lr=lr, X_val=Xval if n_val else None,
-                                                y_val=yval if n_val else None, patience=patience)
+                                                y_val=yval if n_val else None, patience=patience,
+                                                after_epoch=after_epoch)
         spe = -(-Xfit.shape[0] // batch)
         last = losses[(tinfo["epochs_run"] - 1) * spe:tinfo["epochs_run"] * spe]
         sizes = np.array([min(batch, Xfit.shape[0] - k * batch) for k in range(spe)], float)
@@ -183,16 +209,15 @@ def run_cv(kind, dps, n_reps, seed, n_clients=None, window=100, L=None, n_steps=
         ym, ys = _mlp.standardizer(yfit)
         norm = (xm, xs, ym[0], ys[0])
         tinfo, loss = dict(val_losses=np.array([]), epochs_run=0, best_epoch=0), float("nan")
+    screened = bool(tinfo.get("stopped_by_callback"))
     rho2 = None
     if n_val >= 2:
-        g_val = _mlp.f32(_mlp.predict(theta, Xval, norm, d_in)).reshape(n_dp, n_val)
-        g_fit = _mlp.f32(_mlp.predict(theta, Xfit, norm, d_in)).reshape(n_dp, n_fit)
-        rho2 = within_rho2(Y[:, n_fit:n_train], g_val, Y[:, :n_fit], g_fit)
+        rho2 = screen["rho2"] if screened else val_rho2(theta, norm)
     M = int(m_ctrl) if m_ctrl else control_runs(rho2, n_held)
     ratio = var_ratio(rho2, n_reps, n_held, M) if rho2 is not None else None
     info = dict(loss=loss, val_rho2=rho2, var_ratio=ratio, m_ctrl=M, theta=theta, norm=norm,
-                declined=False, **tinfo)
-    if gate and ratio is not None and ratio >= 1.0:
+                declined=False, screened=screened, **tinfo)
+    if gate and ratio is not None and (screened or ratio >= 1.0):
         info.update(declined=True, m_ctrl=0)
         cv = [dict(n=p["n"], m=0, beta=0.0, mean=p["mean"], var=p["var"] / p["n"],
                    half_width=p["half_width"], t_crit=p["t_crit"]) for p in plain]

@@ -188,14 +188,16 @@ def adam_step(theta, m, v, g, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def train(X, y, d_in, seed, epochs, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
-          eps=1e-8, master_fp32=True, X_val=None, y_val=None, patience=0):
+          eps=1e-8, master_fp32=True, X_val=None, y_val=None, patience=0, after_epoch=None):
     """Full training run in FP64 (masters rounded to FP32 after each step when
     master_fp32).  With a validation set (X_val, y_val; standardised with the
     training set's moments) the mean squared error over it is taken after
     every epoch; the parameters of the epoch with the lowest value are kept,
     and training stops after `patience` epochs without a lower value
-    (0: never).  Returns (theta, (x_mean, x_std, y_mean, y_std), losses,
-    info) with info = {val_losses, epochs_run, best_epoch}."""
+    (0: never).  after_epoch(e, theta, norm), called after epoch e (1-based)
+    with the parameters kept so far, may return True to stop.  Returns
+    (theta, (x_mean, x_std, y_mean, y_std), losses, info) with
+    info = {val_losses, epochs_run, best_epoch, stopped_by_callback}."""
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64).reshape(-1)
     xm, xs = standardizer(X)
@@ -213,6 +215,8 @@ def train(X, y, d_in, seed, epochs, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
     t = 0
     losses, val_losses = [], []
     best, best_theta, best_epoch, bad, epochs_run = math.inf, theta, 0, 0, 0
+    stopped = False
+    norm = (xm, xs, ym[0], ys[0])
     for e in range(epochs):
         order = batch_order(n, e, seed)
         for k in range(0, n, batch):
@@ -234,12 +238,16 @@ def train(X, y, d_in, seed, epochs, batch=1024, lr=1e-3, beta1=0.9, beta2=0.999,
                 bad += 1
                 if patience > 0 and bad >= patience:
                     break
+        if after_epoch is not None and after_epoch(e + 1, best_theta if have_val else theta, norm):
+            stopped = True
+            break
     if have_val:
         theta = best_theta
     else:
         best_epoch = epochs_run
-    info = dict(val_losses=np.array(val_losses), epochs_run=epochs_run, best_epoch=best_epoch)
-    return theta, (xm, xs, ym[0], ys[0]), np.array(losses), info
+    info = dict(val_losses=np.array(val_losses), epochs_run=epochs_run, best_epoch=best_epoch,
+                stopped_by_callback=stopped)
+    return theta, norm, np.array(losses), info
 
 
 def predict(theta, X, norm, d_in):

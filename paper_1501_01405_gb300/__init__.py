@@ -231,20 +231,23 @@ def mrip_adam_step(theta, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps
 
 def mrip_mlp_train(d_in, x, y, theta, batch, epochs, order_seed, lr=1e-3, beta1=0.9, beta2=0.999,
                    eps=1e-8, max_steps=0, patience=0, xv=None, yv=None, losses=None, grad=None,
-                   m=None, v=None, val_losses=None, stream=None):
+                   m=None, v=None, val_losses=None, epoch0=0, m_in=None, v_in=None, stream=None):
     """Tensor-core training (synchronous).  x: float (d_in, n) planes; xv, yv
-    the optional validation set.  Returns (epochs run, epoch kept, steps run)."""
+    the optional validation set; epoch0, m_in, v_in resume a run.  Returns
+    (epochs run, epoch kept, steps run)."""
     t = _t()
     n = x.shape[1]
     n_val = 0 if xv is None else xv.shape[1]
     prm = mrip_train_params(batch=int(batch), epochs=int(epochs), patience=int(patience),
                             max_steps=int(max_steps), lr=lr, beta1=beta1, beta2=beta2, eps=eps,
-                            order_seed=int(order_seed))
+                            order_seed=int(order_seed), epoch0=int(epoch0))
     info = (ctypes.c_int32 * 3)()
     _check(lib().mrip_mlp_train(int(d_in), _dev(x, t.float32, "x"), _dev(y, t.float32, "y"), n,
                                 _dev(xv, t.float32, allow_none=True),
                                 _dev(yv, t.float32, allow_none=True), n_val, ctypes.byref(prm),
                                 _dev(theta, t.float32, "theta"),
+                                _dev(m_in, t.float32, allow_none=True),
+                                _dev(v_in, t.float32, allow_none=True),
                                 _dev(losses, t.float32, allow_none=True),
                                 _dev(grad, t.float32, allow_none=True),
                                 _dev(m, t.float32, allow_none=True),
@@ -366,7 +369,8 @@ def mrip_run_cv(model, design_points, n_reps, seed, train_frac=0.1, val_frac=0.1
                 patience=3, batch=1024, gate=True, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                 m_ctrl=0, conf=0.95, net_seed=None):
     """Returns (plain intervals, control-variate intervals, report dict);
-    m_ctrl = 0 lets the library size the control runs."""
+    m_ctrl = 0 lets the library size the control runs; report["declined"] is
+    0 (kept), 1 (declined after training) or 2 (declined by the screen)."""
     a, p = _host(design_points, np.float64)
     n_dp = a.shape[0]
     prm = mrip_cv_params(train_frac=train_frac, val_frac=val_frac, epochs=epochs, patience=patience,
@@ -379,7 +383,6 @@ def mrip_run_cv(model, design_points, n_reps, seed, train_frac=0.1, val_frac=0.1
     _check(lib().mrip_run_cv(model, p, n_dp, int(n_reps), int(seed), ctypes.byref(prm), plain,
                              cv, ctypes.byref(rep)))
     report = {name: getattr(rep, name) for name, _ in mrip_cv_report._fields_}
-    report["declined"] = bool(report["declined"])
     return [_stat_dict(plain[i]) for i in range(n_dp)], [_cv_dict(cv[i]) for i in range(n_dp)], \
         report
 

@@ -53,7 +53,8 @@ class mrip_walk_params(ctypes.Structure):
 class mrip_train_params(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int32), ("patience", ctypes.c_int32),
                 ("max_steps", ctypes.c_int64), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
-                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("order_seed", ctypes.c_uint64)]
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("order_seed", ctypes.c_uint64),
+                ("epoch0", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class mrip_cv_params(ctypes.Structure):
@@ -122,7 +123,7 @@ SIGNATURES = {
     "mrip_mlp_loss_grad": (_INT, [_P, _I32, _P, _P, _I64, _P, _I64, _P, _P, _P]),
     "mrip_adam_step": (_INT, [_P, _P, _P, _P, _I64, _I64, _F, _F, _F, _F, _P]),
     "mrip_mlp_train": (_INT, [_I32, _P, _P, _I64, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
-                              _P]),
+                              _P, _P, _P]),
     "mrip_cv_reduce": (_INT, [_P, _P, _I64, _P, _I64, _I32, _P, _P]),
 }
 

@@ -27,6 +27,7 @@
 //      Var = s_r^2 / n + beta^2 Var(g_ctrl) / M, t on n - 2 degrees of freedom.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <numeric>
 #include <vector>
 
@@ -228,7 +229,7 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const double cells = tandem ? 0.0 : static_cast<double>(m->ff.L) * m->ff.L;
 
     DevBuf feat_all, x_fit, y_fit, x_val, y_val, x_ho, y_ho, ms_dev, tmp, xs_fit, ys_fit, xs_val, ys_val, xs_ho,
-        g_val, g_vald, g_fit, g_fitd, g_ho, g_hod, losses, val_losses, wsums, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
+        g_val, g_vald, g_fit, g_fitd, g_ho, g_hod, losses, val_losses, wsums, adam, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
     const double* feat_src;  // d_in planes of `items`
     const double* y_src;     // items
     if (tandem) {
@@ -288,13 +289,20 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     s = launch_status("cv: standardise");
     if (s != MRIP_OK) return s;
 
-    // 3. training (early stop on the validation set), validation rho^2
+    // 3. training (early stop on the validation set), validation rho^2.
+    //    With the gate on, the first ceil(64 / steps per epoch) epochs run
+    //    alone (at least 64 Adam steps); a validation rho^2 below a quarter
+    //    of the break-even value (with M sized as below, the control variate
+    //    needs rho^2 > 1 - n_held / (1.1 n_reps)) then declines at once;
+    //    otherwise training resumes from that point (parameters, Adam state,
+    //    best validation loss and epochs since) exactly as one run would go on.
     const long long P = mlp_params(d_in);
     const long long B = p->batch;
     const long long spe = (n_f + B - 1) / B;
     const long long n_steps = spe * p->epochs;
     if (!m->cv_theta.ensure(P * sizeof(float)) || !losses.ensure(n_steps * sizeof(float)) ||
-        !val_losses.ensure(static_cast<size_t>(p->epochs) * sizeof(float)))
+        !val_losses.ensure(static_cast<size_t>(p->epochs) * sizeof(float)) ||
+        !adam.ensure(5 * P * sizeof(float)))
         return fail(MRIP_ENOMEM, "cv: network buffers");
     float* theta = m->cv_theta.as<float>();
     m->cv_d_in = 0;  // valid again once training succeeded
@@ -309,7 +317,9 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     sp.Yv = n_v > 0 ? ys_val.as<float>() : nullptr;
     sp.n_val = n_v;
     sp.B = B;
-    sp.epochs = p->epochs;
+    const int screen_epochs = static_cast<int>(std::min<long long>(p->epochs, (64 + spe - 1) / spe));
+    const bool screen_first = p->gate && n_v > 0 && n_val >= 2 && screen_epochs < p->epochs;
+    sp.epochs = screen_first ? screen_epochs : p->epochs;
     sp.patience = p->patience;
     sp.order_seed = p->net_seed;
     sp.lr = p->lr;
@@ -319,21 +329,98 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     sp.theta = theta;
     sp.losses = losses.as<float>();
     sp.val_losses = n_v > 0 ? val_losses.as<float>() : nullptr;
+    sp.m_out = adam.as<float>();
+    sp.v_out = adam.as<float>() + P;
+    sp.theta_last = adam.as<float>() + 4 * P;
     TrainInfo info{};
     s = mlp_train(sp, &info, st);
     if (s != MRIP_OK) return s;
     m->cv_d_in = d_in;
     m->cv_norm = ms;
-    R.epochs_run = info.epochs_run;
-    R.best_epoch = info.best_epoch;
+    int epochs_run = info.epochs_run, best_epoch = info.best_epoch;
+    float v_best = std::numeric_limits<float>::infinity();
+    if (n_v > 0 && best_epoch > 0) {
+        cudaError_t e = cudaMemcpyAsync(&v_best, val_losses.as<float>() + (best_epoch - 1), sizeof(float),
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e, "cv: validation loss read");
+    }
+    // the pooled within-design-point rho^2 of the current network on the
+    // validation replications (each design point scaled by its fit set)
+    auto validation_rho2 = [&](double& out) -> mrip_status {
+        out = std::nan("");
+        if (!(n_v > 0 && n_val >= 2)) return MRIP_OK;
+        if (!g_fit.ensure(n_f * sizeof(float)) || !g_fitd.ensure(n_f * sizeof(double)))
+            return fail(MRIP_ENOMEM, "cv: fit predictions");
+        mrip_status r = mlp_forward(theta, d_in, xs_val.as<float>(), n_v, g_val.as<float>(), st);
+        if (r == MRIP_OK) r = mlp_forward(theta, d_in, xs_fit.as<float>(), n_f, g_fit.as<float>(), st);
+        if (r != MRIP_OK) return r;
+        to_double<<<blocks(n_v), kT, 0, st>>>(g_val.as<float>(), n_v, g_vald.as<double>());
+        to_double<<<blocks(n_f), kT, 0, st>>>(g_fit.as<float>(), n_f, g_fitd.as<double>());
+        within_dp_sums<<<ceil_div_u(n_dp, 128), 128, 0, st>>>(y_val.as<double>(), g_vald.as<double>(), n_val,
+                                                             y_fit.as<double>(), g_fitd.as<double>(), n_fit,
+                                                             n_dp, wsums.as<double>());
+        r = launch_status("cv: validation correlation");
+        if (r != MRIP_OK) return r;
+        std::vector<double> h(3 * static_cast<size_t>(n_dp));
+        cudaError_t e = cudaMemcpyAsync(h.data(), wsums.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_status(e, "cv: validation correlation");
+        double syg = 0.0, syy = 0.0, sgg = 0.0;
+        for (int32_t d = 0; d < n_dp; ++d) {  // design points in order
+            syg += h[3 * d];
+            syy += h[3 * d + 1];
+            sgg += h[3 * d + 2];
+        }
+        out = (syy > 0.0 && sgg > 0.0) ? (syg * syg) / (syy * sgg) : 0.0;
+        return MRIP_OK;
+    };
+    double rho2 = std::nan("");
+    const double rho2_be = 1.0 - static_cast<double>(n_held) / (1.1 * static_cast<double>(n_reps));
+    bool screened = false;
+    // a first part that ran to its end (no early stop inside) is screened
+    if (screen_first && epochs_run == screen_epochs) {
+        s = validation_rho2(rho2);
+        if (s != MRIP_OK) return s;
+        screened = rho2 >= 0.0 && rho2 < 0.25 * rho2_be;
+        if (!screened) {
+            const int e0 = epochs_run;
+            TrainSpec rest = sp;
+            rest.epochs = p->epochs - e0;
+            rest.epoch0 = e0;
+            rest.theta_in = adam.as<float>() + 4 * P;  // the trajectory, not the kept epoch
+            rest.theta_last = nullptr;
+            rest.m_in = adam.as<float>();
+            rest.v_in = adam.as<float>() + P;
+            rest.m_out = adam.as<float>() + 2 * P;
+            rest.v_out = adam.as<float>() + 3 * P;
+            rest.losses = losses.as<float>() + e0 * spe;
+            rest.val_losses = val_losses.as<float>() + e0;
+            rest.best0 = v_best;
+            rest.bad0 = e0 - best_epoch;
+            TrainInfo more{};
+            s = mlp_train(rest, &more, st);
+            if (s != MRIP_OK) return s;
+            epochs_run = e0 + more.epochs_run;
+            if (more.best_epoch > 0) best_epoch = e0 + more.best_epoch;
+            rho2 = std::nan("");
+        }
+    }
+    if (!screened) {
+        s = validation_rho2(rho2);  // of the kept network
+        if (s != MRIP_OK) return s;
+    }
+    long long last0 = 0;  // first step of the last epoch run, in `losses`
+    last0 = static_cast<long long>(epochs_run > 0 ? epochs_run - 1 : 0) * spe;
+    R.epochs_run = epochs_run;
+    R.best_epoch = best_epoch;
     {   // mean minibatch loss of the last epoch run, and the kept epoch's validation loss
-        const long long last = static_cast<long long>(info.epochs_run > 0 ? info.epochs_run - 1 : 0) * spe;
         std::vector<float> hl(spe);
-        cudaError_t e = cudaMemcpyAsync(hl.data(), losses.as<float>() + last, spe * sizeof(float),
+        cudaError_t e = cudaMemcpyAsync(hl.data(), losses.as<float>() + last0, spe * sizeof(float),
                                         cudaMemcpyDeviceToHost, st);
         float vl = std::nanf("");
-        if (e == cudaSuccess && n_v > 0 && info.best_epoch > 0)
-            e = cudaMemcpyAsync(&vl, val_losses.as<float>() + (info.best_epoch - 1), sizeof(float),
+        if (e == cudaSuccess && n_v > 0 && best_epoch > 0)
+            e = cudaMemcpyAsync(&vl, val_losses.as<float>() + (best_epoch - 1), sizeof(float),
                                 cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_status(e, "cv: loss read");
@@ -346,34 +433,6 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
         R.train_loss = static_cast<float>(acc / wsum);
         R.val_loss = vl;
     }
-    double rho2 = std::nan("");
-    if (n_v > 0 && n_val >= 2) {
-        // predictions of the validation and fit replications (the fit set
-        // gives each design point's scales)
-        if (!g_fit.ensure(n_f * sizeof(float)) || !g_fitd.ensure(n_f * sizeof(double)))
-            return fail(MRIP_ENOMEM, "cv: fit predictions");
-        s = mlp_forward(theta, d_in, xs_val.as<float>(), n_v, g_val.as<float>(), st);
-        if (s == MRIP_OK) s = mlp_forward(theta, d_in, xs_fit.as<float>(), n_f, g_fit.as<float>(), st);
-        if (s != MRIP_OK) return s;
-        to_double<<<blocks(n_v), kT, 0, st>>>(g_val.as<float>(), n_v, g_vald.as<double>());
-        to_double<<<blocks(n_f), kT, 0, st>>>(g_fit.as<float>(), n_f, g_fitd.as<double>());
-        within_dp_sums<<<ceil_div_u(n_dp, 128), 128, 0, st>>>(y_val.as<double>(), g_vald.as<double>(), n_val,
-                                                             y_fit.as<double>(), g_fitd.as<double>(), n_fit,
-                                                             n_dp, wsums.as<double>());
-        s = launch_status("cv: validation correlation");
-        if (s != MRIP_OK) return s;
-        std::vector<double> h(3 * static_cast<size_t>(n_dp));
-        cudaError_t e = cudaMemcpyAsync(h.data(), wsums.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_status(e, "cv: validation correlation");
-        double syg = 0.0, syy = 0.0, sgg = 0.0;
-        for (int32_t d = 0; d < n_dp; ++d) {  // design points in order
-            syg += h[3 * d];
-            syy += h[3 * d + 1];
-            sgg += h[3 * d + 2];
-        }
-        rho2 = (syy > 0.0 && sgg > 0.0) ? (syg * syg) / (syy * sgg) : 0.0;
-    }
     R.val_rho2 = rho2;
     const long long M = p->m_ctrl > 0 ? p->m_ctrl : control_runs(rho2, n_held);
     if (rho2 >= 0.0)
@@ -381,8 +440,8 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
                       ((1.0 - rho2) / static_cast<double>(n_held) + rho2 / static_cast<double>(M));
     timer.mark();
 
-    if (p->gate && R.var_ratio >= 1.0) {  // the plain estimator stays
-        R.declined = 1;
+    if (p->gate && (screened || R.var_ratio >= 1.0)) {  // the plain estimator stays
+        R.declined = screened ? 2 : 1;
         R.m_ctrl = 0;
         for (int32_t d = 0; d < n_dp; ++d) {
             mrip_cv_stat& o = cv_out[d];

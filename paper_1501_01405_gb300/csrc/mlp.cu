@@ -386,6 +386,12 @@ struct TrainArgs {
     int patience;       // > 0: stop after this many epochs without a lower validation loss
     float* val_losses;  // per epoch (may be null)
     int* info;          // may be null: epochs run, epoch kept, steps run
+    const float* m_in;  // may be null (zero): Adam's moments to resume from
+    const float* v_in;
+    float best0;        // validation loss to beat (+inf: none yet)
+    int bad0;           // epochs without a lower validation loss so far
+    const float* theta_in;  // may be null (= theta): the parameters to start from
+    float* theta_last;      // may be null: the parameters after the last step run
 };
 
 // ---------------------------------------------------------------------------
@@ -481,10 +487,12 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
 
     if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
     if (t == 0) tc::mbar_init(&S.bar);
-    for (int i = t; i < P; i += kTcThreads) th[i] = ta.theta[i];
+    const float* th_src = ta.theta_in ? ta.theta_in : ta.theta;
+    for (int i = t; i < P; i += kTcThreads) th[i] = th_src[i];
     for (int i = t; i < slice; i += kTcThreads) {
-        mom[i] = 0.0f;
-        vel[i] = 0.0f;
+        const int p = p_lo + i;
+        mom[i] = (ta.m_in && p < P) ? ta.m_in[p] : 0.0f;
+        vel[i] = (ta.v_in && p < P) ? ta.v_in[p] : 0.0f;
     }
     for (int i = t; i < kTcRows * kTcRows * 2 / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(S.dz2tt)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -615,8 +623,8 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
 
     long long step = 0;
     bool stop = false;
-    float best = __int_as_float(0x7f800000);  // +inf
-    int bad = 0, best_epoch = 0, epochs_run = 0;
+    float best = ta.best0;
+    int bad = ta.bad0, best_epoch = 0, epochs_run = 0;
     for (int ep = 0; ep < ta.epochs && !stop; ++ep) {
         const SampleMap map{nullptr, ta.ab[2 * ep], ta.ab[2 * ep + 1], static_cast<unsigned long long>(ta.n_tr), 0};
         for (long long off = 0; off < ta.n_tr; off += ta.B, ++step) {
@@ -815,6 +823,8 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     }
     if (ta.n_val == 0)
         for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta[p] = th[p];
+    if (ta.theta_last)
+        for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.theta_last[p] = th[p];
     if (ta.m_out)
         for (int p = p_lo + t; p < p_hi; p += kTcThreads) ta.m_out[p] = mom[p - p_lo];
     if (ta.v_out)
@@ -1027,14 +1037,17 @@ mrip_status mlp_train(const TrainSpec& sp, TrainInfo* info, cudaStream_t st) {
     const long long spe = (sp.n + sp.B - 1) / sp.B;
     long long n_steps = spe * sp.epochs;
     if (sp.max_steps > 0 && sp.max_steps < n_steps) n_steps = sp.max_steps;
+    // resuming at epoch epoch0: its order and Adam's step count continue
+    const long long step0 = static_cast<long long>(sp.epoch0) * spe;
     std::vector<unsigned long long> ab(2 * static_cast<size_t>(sp.epochs));
     for (int ep = 0; ep < sp.epochs; ++ep)
-        epoch_affine(sp.order_seed, ep, static_cast<unsigned long long>(sp.n), ab[2 * ep], ab[2 * ep + 1]);
+        epoch_affine(sp.order_seed, sp.epoch0 + ep, static_cast<unsigned long long>(sp.n), ab[2 * ep],
+                     ab[2 * ep + 1]);
     std::vector<float> bc(2 * static_cast<size_t>(n_steps));
     for (long long k = 1; k <= n_steps; ++k) {
-        bc[2 * (k - 1)] = static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta1), static_cast<double>(k)));
-        bc[2 * (k - 1) + 1] =
-            static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta2), static_cast<double>(k)));
+        const double kk = static_cast<double>(step0 + k);
+        bc[2 * (k - 1)] = static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta1), kk));
+        bc[2 * (k - 1) + 1] = static_cast<float>(1.0 - std::pow(static_cast<double>(sp.beta2), kk));
     }
     // scratch: [info 16 B, timeout flag 16 B][ab][bc]
     const size_t ab_bytes = ab.size() * sizeof(unsigned long long);
@@ -1055,7 +1068,8 @@ mrip_status mlp_train(const TrainSpec& sp, TrainInfo* info, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_status(e, "mlp train: shared memory attribute");
     TrainArgs ta{sp.X, sp.Y, sp.n, sp.B, spe, sp.epochs, sp.d_in, d_ab, d_bc, sp.lr, sp.beta1, sp.beta2, sp.eps,
                  sp.theta, sp.losses, sp.max_steps, sp.grad, sp.m_out, sp.v_out, sp.Xv, sp.Yv,
-                 sp.Xv ? sp.n_val : 0, sp.patience, sp.val_losses, d_info};
+                 sp.Xv ? sp.n_val : 0, sp.patience, sp.val_losses, d_info, sp.m_in, sp.v_in,
+                 sp.best0, sp.bad0, sp.theta_in, sp.theta_last};
     mlp_train_tc_kernel<<<kTcCluster, kTcThreads, smem, st>>>(ta, flag);
     mrip_status s = launch_status("mlp train (tensor cores)");
     if (s != MRIP_OK) return s;
@@ -1131,12 +1145,13 @@ extern "C" mrip_status mrip_adam_step(float* d_theta, float* d_m, float* d_v, co
 
 extern "C" mrip_status mrip_mlp_train(int32_t d_in, const float* d_x, const float* d_y, int64_t n,
                                       const float* d_xv, const float* d_yv, int64_t n_val,
-                                      const mrip_train_params* prm, float* d_theta, float* d_losses,
-                                      float* d_grad, float* d_m, float* d_v, float* d_val_losses,
-                                      int32_t* info_out, void* stream) {
+                                      const mrip_train_params* prm, float* d_theta, const float* d_m_in,
+                                      const float* d_v_in, float* d_losses, float* d_grad, float* d_m,
+                                      float* d_v, float* d_val_losses, int32_t* info_out, void* stream) {
     if (d_in < 1 || d_in > kMaxIn || n < 1 || n_val < 0 || !prm)
         return fail(MRIP_EINVAL, "mrip_mlp_train: d_in in 1..8, n >= 1, n_val >= 0, params");
-    if (prm->batch < 1 || prm->epochs < 1 || prm->patience < 0 || prm->max_steps < 0 || !(prm->lr > 0.0f) ||
+    if (prm->batch < 1 || prm->epochs < 1 || prm->epoch0 < 0 || prm->patience < 0 || prm->max_steps < 0 ||
+        !(prm->lr > 0.0f) ||
         !(prm->beta1 >= 0.0f && prm->beta1 < 1.0f) || !(prm->beta2 >= 0.0f && prm->beta2 < 1.0f) ||
         !(prm->eps > 0.0f))
         return fail(MRIP_EINVAL, "mrip_mlp_train: batch, epochs >= 1, patience, max_steps >= 0, lr, eps > 0, "
@@ -1154,6 +1169,9 @@ extern "C" mrip_status mrip_mlp_train(int32_t d_in, const float* d_x, const floa
     sp.n_val = n_val;
     sp.B = prm->batch;
     sp.epochs = prm->epochs;
+    sp.epoch0 = prm->epoch0;
+    sp.m_in = d_m_in;
+    sp.v_in = d_v_in;
     sp.max_steps = prm->max_steps;
     sp.patience = prm->patience;
     sp.order_seed = prm->order_seed;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <limits>
 #include <vector>
 
 #include "../../include/mrip.h"
@@ -125,6 +126,13 @@ struct TrainSpec {
     float* m_out;
     float* v_out;
     float* val_losses;
+    int epoch0 = 0;               // resume at this epoch (order and step count continue)
+    const float* m_in = nullptr;  // Adam's moments to resume from (null: zero)
+    const float* v_in = nullptr;
+    float best0 = std::numeric_limits<float>::infinity();  // validation loss to beat
+    int bad0 = 0;                       // epochs without a lower validation loss so far
+    const float* theta_in = nullptr;    // start from these (null: theta)
+    float* theta_last = nullptr;        // the parameters after the last step (may be null)
 };
 struct TrainInfo {
     int epochs_run, best_epoch, steps;

@@ -165,7 +165,12 @@ def _compare_pipeline(m, kind, dps, n_reps, seed, model_kw, kw, threads):
     assert norm[-1, 0] == pytest.approx(ym, rel=1e-12) and norm[-1, 1] == pytest.approx(ys, rel=1e-12)
     if info["val_rho2"] is not None:
         assert rep["val_rho2"] == pytest.approx(info["val_rho2"], abs=2e-3)
-    assert rep["declined"] == info["declined"]
+    if rep["declined"] == 2:  # the screen (the GPU's network is the screened one)
+        n_train = math.ceil(kw["train_frac"] * n_reps)
+        assert rep["epochs_run"] < kw["epochs"]
+        assert info["val_rho2"] < 0.25 * (1 - (n_reps - n_train) / (1.1 * n_reps)) + 2e-3
+    else:
+        assert bool(rep["declined"]) == info["declined"]
     assert rep["m_ctrl"] == info["m_ctrl"] or abs(rep["m_ctrl"] - info["m_ctrl"]) <= \
         0.02 * info["m_ctrl"] + 1
     if rep["m_ctrl"] == info["m_ctrl"]:
@@ -245,21 +250,28 @@ def test_run_cv_validation_gate_accepts_informative_window(env):
 
 def test_run_cv_gate_declines_uninformative_window(env):
     """2,000 clients and a 10-client window: the early window says almost
-    nothing about the replication mean, so the predicted variance ratio is
-    >= 1 and the plain intervals are returned as the control-variate
-    result, with no control runs."""
+    nothing about the replication mean, so the validation rho^2 after the
+    screen's 64 Adam steps is far below the break-even and the plain
+    intervals are returned as the control-variate result, with no further
+    training and no control runs."""
     eng, torch = env
     dps = mrip_inputs.tandem_design_points(64, seed=6)
-    kw = dict(train_frac=0.1, val_frac=0.2, epochs=10, patience=2, batch=256, lr=1e-3,
+    kw = dict(train_frac=0.2, val_frac=0.25, epochs=10, patience=2, batch=32, lr=1e-3,
               m_ctrl=0, gate=True)
     m = eng.Model(eng.MRIP_TANDEM3, n_clients=2000, window=10)
-    plain, cv, rep = m.run_cv(dps, 100, 8, **kw)
+    plain, cv, rep = m.run_cv(dps, 200, 8, **kw)
     assert rep["declined"] and rep["m_ctrl"] == 0 and rep["var_ratio"] >= 1.0
+    # 64 x 30 fit samples in minibatches of 32 = 60 steps per epoch, so the
+    # screen comes after 2 epochs; with 10 validation replications per design
+    # point (576 degrees of freedom) its rho^2 is far below a quarter of the
+    # break-even 1 - 160 / 220 = 0.27: declined there, no more training
+    assert rep["declined"] == 2 and rep["epochs_run"] == 2
+    assert rep["val_rho2"] < 0.25 * (1 - 160 / 220)
     for p, c in zip(plain, cv):
         assert c["mean"] == p["mean"] and c["half_width"] == p["half_width"] and c["m"] == 0
     assert rep["ms_control"] == 0.0 and rep["ms_infer"] == 0.0
     theta, _ = m.cv_network()
-    _, _, info = ocv.run_cv("tandem3", dps, 100, 8, n_clients=2000, window=10,
+    _, _, info = ocv.run_cv("tandem3", dps, 200, 8, n_clients=2000, window=10,
                             theta=theta.astype(np.float64), threads=oracle.host_threads(), **kw)
     assert info["declined"]
     assert rep["val_rho2"] == pytest.approx(info["val_rho2"], abs=2e-3)

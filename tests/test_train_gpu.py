@@ -164,3 +164,21 @@ def test_validation_and_early_stop(env, case):
         yhat, _ = omlp.forward(th, Xv, d_in)
         ref = float(np.mean((yhat - yv) ** 2))
         assert val[e - 1] == pytest.approx(ref, rel=1e-4), e
+
+
+def test_resume_continues_the_trajectory(env):
+    """One epoch, then the remaining epochs resumed from its parameters and
+    Adam moments (epoch0 = 1), equals one run of all epochs bit for bit."""
+    eng, torch = env
+    d_in, n, batch, epochs, seed = 8, 2100, 512, 4, 12
+    X, y, theta0 = _data(d_in, n, seed)
+    full = _run(eng, torch, d_in, X, y, theta0, batch, epochs, seed, 0)
+    first = _run(eng, torch, d_in, X, y, theta0, batch, 1, seed, 0)
+    dev = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")  # noqa: E731
+    rest = _run(eng, torch, d_in, X, y, first["theta"], batch, epochs - 1, seed, 0, epoch0=1,
+                m_in=dev(first["m"]), v_in=dev(first["v"]))
+    for k in ("theta", "m", "v"):
+        assert np.array_equal(rest[k], full[k]), k
+    spe = -(-n // batch)
+    assert np.array_equal(np.concatenate([first["losses"], rest["losses"]]), full["losses"])
+    assert rest["info"][2] == (epochs - 1) * spe
