@@ -64,7 +64,7 @@ typedef enum {
     MRIP_ECUDA = 3,         /* CUDA runtime or launch error                      */
     MRIP_ESTEPCAP = 4,      /* a replication hit its step cap (output set to -1) */
     MRIP_ESTATE = 5,        /* call out of order (e.g. stats before run)         */
-    MRIP_EUNSUPPORTED = 6   /* valid request this build does not implement       */
+    MRIP_EUNSUPPORTED = 6   /* valid request this library does not implement     */
 } mrip_status;
 
 typedef enum {
@@ -200,7 +200,7 @@ mrip_status mrip_autotune(mrip_model *model, const double *design_points, int32_
                           int64_t n_reps, uint64_t seed, int trials, const char *cache_path);
 
 /* Learned control variate (engine extension; the paper's estimator is the
- * plain mean of Section 1, which stays the fallback and the judge).
+ * plain mean of Section 1, which stays the fallback and the yardstick).
  * Synchronous.  Steps:
  *   1. runs the n_reps replications of every design point and writes the
  *      plain intervals (all n_reps) into plain_out;
