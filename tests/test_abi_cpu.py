@@ -136,3 +136,47 @@ def test_plan_json_round_trip_and_rejection():
         q.stats()
     m.close()
     q.close()
+
+
+def test_cv_and_training_arguments_rejected_on_host():
+    """mrip_run_cv and mrip_mlp_train validate their parameters before any
+    device work: a bad training fraction, validation fraction, patience or
+    control-run count, too few held-out or fit replications, a model kind
+    without a control variate; a bad network size, minibatch or resume
+    epoch."""
+    eng = _engine()
+    dps = [[0.9, 1.0, 1.1, 1.2]]
+    m = eng.Model(eng.MRIP_TANDEM3, n_clients=50, window=10)
+    bad = [dict(train_frac=0.0), dict(train_frac=1.0), dict(val_frac=1.0), dict(val_frac=-0.1),
+           dict(patience=-1), dict(m_ctrl=1), dict(epochs=0), dict(batch=0), dict(conf=1.0)]
+    for kw in bad:
+        with pytest.raises(eng.MripError) as e:
+            m.run_cv(dps, 40, 7, **kw)
+        assert e.value.code == 1, kw
+    with pytest.raises(eng.MripError) as e:  # 4 replications: 1 training, 3 held-out, 0 fit left
+        m.run_cv(dps, 4, 7, train_frac=0.25, val_frac=0.5)
+    assert e.value.code == 1 and b"fit" in eng.lib().mrip_last_error()
+    with pytest.raises(eng.MripError) as e:
+        m.cv_network()
+    assert e.value.code == 5  # no control-variate run yet
+    m.close()
+    w = eng.Model(eng.MRIP_WALK_L1_EXIT, max_steps=1 << 20)
+    with pytest.raises(eng.MripError) as e:
+        w.run_cv([[8.0]], 40, 7)
+    assert e.value.code == 6
+    w.close()
+    L = eng.lib()
+    from paper_1501_01405_gb300 import _abi
+    prm = _abi.mrip_train_params(batch=64, epochs=1, patience=0, max_steps=0, lr=1e-3, beta1=0.9,
+                                 beta2=0.999, eps=1e-8, order_seed=1, epoch0=0)
+    p16 = ctypes.c_void_p(16)
+    assert L.mrip_mlp_train(9, p16, p16, 10, None, None, 0, ctypes.byref(prm), p16, None, None,
+                            None, None, None, None, None, None, None) == 1
+    for field, value in (("batch", 0), ("epochs", 0), ("epoch0", -1), ("lr", 0.0), ("beta2", 1.0)):
+        q = _abi.mrip_train_params.from_buffer_copy(prm)
+        setattr(q, field, value)
+        assert L.mrip_mlp_train(8, p16, p16, 10, None, None, 0, ctypes.byref(q), p16, None, None,
+                                None, None, None, None, None, None, None) == 1, field
+    # a validation set needs its pointers
+    assert L.mrip_mlp_train(8, p16, p16, 10, None, None, 5, ctypes.byref(prm), p16, None, None,
+                            None, None, None, None, None, None, None) == 1
