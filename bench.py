@@ -791,12 +791,13 @@ def time_to_target(eng, torch, stream, seed, which="tandem_cv"):
 
 def config_rates(eng, torch, steps=5, warmup=3):
     """replications/s of the other configurations (device time, CUDA events,
-    L2 flushed between steps): M/M/1 (config 0, one CUDA graph per step), the
-    128^2 forest fire (config 1), the walk batch (config 2) and the plain
-    tandem (config 3)."""
+    L2 flushed between steps): M/M/1 (32 replications, one CUDA graph per
+    step; and 2^16 replications, the throughput row), the 128^2 forest fire,
+    the walk batch and the plain tandem, each with its dominant kernel's
+    roofline fraction over the whole step's time."""
     out = {}
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
-    for name in ("mm1_32", "ff128", "walk8", "tandem"):
+    for name in ("mm1_32", "mm1_64k", "ff128", "walk8", "tandem"):
         wl = make_workload(name, 0)
         wl.setup(eng, torch)
         step = wl.step
@@ -825,8 +826,13 @@ def config_rates(eng, torch, steps=5, warmup=3):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         t = sum(ms) / len(ms)
+        rw = wl.roofline_work()
+        ach = rw["work"] / (t / 1e3) / 1e9  # the whole step's time: a lower bound
         out[name] = {"replications_per_s": wl.units() / (t / 1e3), "ms_per_step": t,
-                     "steps": n, "workload": wl.config()["workload"]}
+                     "steps": n, "workload": wl.config()["workload"],
+                     "roofline": {"kernel": rw["kernel"], "bound": rw["bound"], "unit": rw["unit"],
+                                  "achieved": ach, "peak": rw["peak"], "frac": ach / rw["peak"],
+                                  "per_unit": rw["per_unit"], "timed": "whole step"}}
         del graph
     return out
 

@@ -40,3 +40,24 @@ def test_fewer_than_three_warmup_steps_rejected():
     r = _run("--impl", "reference", "--workload", "mm1_32", "--steps", "1", "--warmup", "2")
     assert r.returncode != 0
     assert "warmup" in (r.stderr + r.stdout)
+
+
+def test_shard_mode_splits_the_replications():
+    """bench.py --shard: every rank runs its own contiguous replication range
+    of the one experiment (same seed), the ranges cover every replication
+    once, and the line's unit count is the whole experiment's."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for name in ("ff256", "ff128", "walk8", "tandem", "mm1_32"):
+        world = 3
+        ranges, full = [], None
+        for r in range(world):
+            wl = bench.make_workload(name, r)
+            n_reps = wl.w["n_reps"]
+            f = wl.shard(r, world)
+            full = f if full is None else full
+            assert f == wl.w["n_dp"] * n_reps
+            assert wl.seed == wl.w["seed"]
+            ranges.append((wl.rep0, wl.rep0 + wl.w["n_reps"]))
+        assert ranges[0][0] == 0 and ranges[-1][1] == n_reps
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
