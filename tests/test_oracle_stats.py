@@ -328,3 +328,27 @@ def test_control_run_sizing_and_gate():
     rho_be = 1 - 230 / (256 * 1.1)
     assert ocv.var_ratio(rho_be + 0.01, 256, 230, ocv.control_runs(rho_be + 0.01, 230)) < 1.0
     assert ocv.var_ratio(rho_be - 0.01, 256, 230, ocv.control_runs(rho_be - 0.01, 230)) > 1.0
+
+
+def test_training_callback_stops_after_the_requested_epoch():
+    """The screen's hook: a callback that asks to stop after epoch 2 ends
+    training there; the parameters are those of a 2-epoch run, the callback
+    saw epochs 1 and 2 with the parameters then kept, and the standardisation
+    it was given is the run's."""
+    rng = np.random.default_rng(13)
+    X = rng.uniform(-1, 1, size=(500, 8))
+    y = X[:, 0] - 2 * X[:, 3] + 0.1 * rng.standard_normal(500)
+    seen = []
+
+    def cb(e, th, norm):
+        seen.append((e, th.copy(), norm))
+        return e == 2
+    theta, norm, losses, info = omlp.train(X, y, 8, 5, epochs=9, batch=100, lr=3e-3,
+                                           after_epoch=cb)
+    assert info["stopped_by_callback"] and info["epochs_run"] == 2 and len(losses) == 10
+    assert [s[0] for s in seen] == [1, 2]
+    ref, _, _, _ = omlp.train(X, y, 8, 5, epochs=2, batch=100, lr=3e-3)
+    assert np.array_equal(theta, ref) and np.array_equal(seen[1][1], ref)
+    one, _, _, _ = omlp.train(X, y, 8, 5, epochs=1, batch=100, lr=3e-3)
+    assert np.array_equal(seen[0][1], one)
+    assert all(np.array_equal(a, b) for a, b in zip(seen[0][2][:2], norm[:2]))
