@@ -26,7 +26,7 @@
 //   tree'    = (tree & ~ignite) | (empty & grow).
 // The burning count of each step is a popcount, a warp reduction and a
 // shared-memory atomic; counts are flushed to global memory every 64 steps
-// (coalesced) from a double-buffered slot array.
+// (coalesced, 16-byte stores where aligned) from a double-buffered slot array.
 #include "common.cuh"
 #include "model.cuh"
 
@@ -78,6 +78,31 @@ __device__ __forceinline__ void or_if_below(uint32_t& bits, uint32_t w, uint32_t
     asm("{\n .reg .pred p;\n setp.lt.u32 p, %1, %2;\n @p or.b32 %0, %0, %3;\n}\n"
         : "+r"(bits)
         : "r"(w), "r"(t), "r"(bit));
+}
+
+// Flush the n_slot (<= 64) burning counts of one 64-step chunk from the
+// shared slot array to dst (skipped when null) and add them to my_sum,
+// clearing the slots when asked.  Where dst is 16-byte aligned and n_slot a
+// multiple of 4 (every chunk when n_steps is), a thread moves four counts
+// with one 16-byte store.
+template <int TPB>
+__device__ __forceinline__ void ff_flush(int* slot, int n_slot, int32_t* dst, bool clear, long long& my_sum) {
+    if (dst && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 && (n_slot & 3) == 0) {
+        for (int s4 = threadIdx.x; s4 < (n_slot >> 2); s4 += TPB) {
+            int4* src = reinterpret_cast<int4*>(slot) + s4;
+            const int4 v = *src;
+            if (clear) *src = make_int4(0, 0, 0, 0);
+            my_sum += static_cast<long long>(v.x) + v.y + v.z + v.w;
+            reinterpret_cast<int4*>(dst)[s4] = v;
+        }
+    } else {
+        for (int s = threadIdx.x; s < n_slot; s += TPB) {
+            const int v = slot[s];
+            if (clear) slot[s] = 0;
+            my_sum += v;
+            if (dst) dst[s] = v;
+        }
+    }
 }
 
 // Threads per CTA for a lattice of W words per row.
@@ -176,7 +201,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
     constexpr int TPB = ff_threads<W>();
     constexpr int NWARP = TPB / 32;
     extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD]
-    __shared__ int cnt[2][64];
+    __shared__ __align__(16) int cnt[2][64];
     __shared__ long long red[NWARP];
 
     const int lane = threadIdx.x & 31;
@@ -239,12 +264,8 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
         if ((t & 63) == 0 || t == n_steps) {
             const int chunk = (t - 1) >> 6;
             const int n_slot = t - chunk * 64;
-            for (int s = threadIdx.x; s < n_slot; s += TPB) {
-                const int v = cnt[chunk & 1][s];
-                cnt[chunk & 1][s] = 0;
-                my_sum += v;
-                if (counts) counts[item * n_steps + chunk * 64 + s] = v;
-            }
+            ff_flush<TPB>(cnt[chunk & 1], n_slot, counts ? counts + item * n_steps + chunk * 64 : nullptr, true,
+                          my_sum);
         }
     }
 
@@ -472,7 +493,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
     constexpr int NEV = ev_buffers<W>();
     extern __shared__ uint32_t lattice[];  // [buffer][plane T, B][NWORD], then events [NEV][G, H][NWORD]
     uint32_t* events = lattice + 4 * NWORD;
-    __shared__ int cnt[2][64];
+    __shared__ __align__(16) int cnt[2][64];
     __shared__ long long red[NWARP];
     __shared__ int tot[2][NWARP];
 
@@ -507,12 +528,8 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
         // counts of the steps before t are complete: flush a finished chunk
         if (t > 1 && ((t - 1) & 63) == 0) {
             const int chunk = (t - 2) >> 6;
-            for (int s = threadIdx.x; s < 64; s += TPB) {
-                const int v = cnt[chunk & 1][s];
-                cnt[chunk & 1][s] = 0;
-                my_sum += v;
-                if (counts) counts[item * n_steps + chunk * 64 + s] = v;
-            }
+            ff_flush<TPB>(cnt[chunk & 1], 64, counts ? counts + item * n_steps + chunk * 64 : nullptr, true,
+                          my_sum);
         }
         const uint32_t* cur_t = lattice + ((t - 1) & 1) * 2 * NWORD;
         const uint32_t* cur_b = cur_t + NWORD;
@@ -547,11 +564,8 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
     if (n_steps > 0) {
         const int chunk = (n_steps - 1) >> 6;
         const int n_slot = n_steps - chunk * 64;
-        for (int s = threadIdx.x; s < n_slot; s += TPB) {
-            const int v = cnt[chunk & 1][s];
-            my_sum += v;
-            if (counts) counts[item * n_steps + chunk * 64 + s] = v;
-        }
+        ff_flush<TPB>(cnt[chunk & 1], n_slot, counts ? counts + item * n_steps + chunk * 64 : nullptr, false,
+                      my_sum);
     }
     if (scalar) ff_store_scalar<NWARP>(my_sum, red, scalar, item, n_steps, L);
     if (final_state) {
