@@ -203,7 +203,7 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const long long n_fit = n_train - n_val;
     if (n_fit < 1 || n_held < 3)
         return fail(MRIP_EINVAL, "mrip_run_cv: need >= 1 fit and >= 3 held-out replications");
-    const long long m_cap = std::max<long long>(10 * n_held, 100 * n_held);
+    const long long m_cap = 100 * n_held;  // the most control runs the sizing asks for
     if (n_reps + std::max<long long>(p->m_ctrl, m_cap) > 0x100000000ll)
         return fail(MRIP_EINVAL, "mrip_run_cv: replication indices < 2^32");
     const bool tandem = m->kind == MRIP_TANDEM3;
@@ -228,8 +228,14 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
     const long long items = static_cast<long long>(n_dp) * n_reps;
     const double cells = tandem ? 0.0 : static_cast<double>(m->ff.L) * m->ff.L;
 
-    DevBuf feat_all, x_fit, y_fit, x_val, y_val, x_ho, y_ho, ms_dev, tmp, xs_fit, ys_fit, xs_val, ys_val, xs_ho,
-        g_val, g_vald, g_fit, g_fitd, g_ho, g_hod, losses, val_losses, wsums, adam, c_y, c_feat, c_counts, xs_c, g_c, g_cd, out5;
+    auto& B_ = m->cvb;  // the handle's buffers: grown on demand, kept between calls
+    DevBuf &feat_all = B_.feat_all, &x_fit = B_.x_fit, &y_fit = B_.y_fit, &x_val = B_.x_val, &y_val = B_.y_val,
+           &x_ho = B_.x_ho, &y_ho = B_.y_ho, &ms_dev = B_.ms_dev, &tmp = B_.tmp, &xs_fit = B_.xs_fit,
+           &ys_fit = B_.ys_fit, &xs_val = B_.xs_val, &ys_val = B_.ys_val, &xs_ho = B_.xs_ho, &g_val = B_.g_val,
+           &g_vald = B_.g_vald, &g_fit = B_.g_fit, &g_fitd = B_.g_fitd, &g_ho = B_.g_ho, &g_hod = B_.g_hod,
+           &losses = B_.losses, &val_losses = B_.val_losses, &wsums = B_.wsums, &adam = B_.adam, &c_y = B_.c_y,
+           &c_feat = B_.c_feat, &c_counts = B_.c_counts, &xs_c = B_.xs_c, &g_c = B_.g_c, &g_cd = B_.g_cd,
+           &out5 = B_.out5;
     const double* feat_src;  // d_in planes of `items`
     const double* y_src;     // items
     if (tandem) {

@@ -57,7 +57,13 @@ struct mrip_model {
     int64_t n_reps = 0;
     int64_t rep0 = 0;  // replication index of output column 0 (mrip_run_range)
     bool has_run = false;
-    // the network of the last mrip_run_cv
+    // the control variate's working buffers (kept between mrip_run_cv calls)
+    // and the network of the last one
+    struct {
+        DevBuf feat_all, x_fit, y_fit, x_val, y_val, x_ho, y_ho, ms_dev, tmp, xs_fit, ys_fit, xs_val, ys_val, xs_ho,
+            g_val, g_vald, g_fit, g_fitd, g_ho, g_hod, losses, val_losses, wsums, adam, c_y, c_feat, c_counts, xs_c,
+            g_c, g_cd, out5;
+    } cvb;
     DevBuf cv_theta;
     std::vector<double> cv_norm;
     int cv_d_in = 0;
