@@ -798,7 +798,15 @@ __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict_
 
     bool fixed_ok = fix_rate_ok(lam) && fix_rate_ok(mu);
     if (fixed_ok) {
-        const unsigned long long cl = fix_scale(lam), cmu = fix_scale(mu);
+        // every thread needs the same two multipliers (FP64 divisions on a
+        // slow pipe): lane 0 of each warp computes them, a shuffle shares them
+        unsigned long long cl = 0, cmu = 0;
+        if (lane == 0) {
+            cl = fix_scale(lam);
+            cmu = fix_scale(mu);
+        }
+        cl = __shfl_sync(kFull, cl, 0);
+        cmu = __shfl_sync(kFull, cmu, 0);
         FixMap f{-kSat, 0};
         long long* st_s = fix_stage + threadIdx.x;
         long long* st_a = fix_stage + k * blockDim.x + threadIdx.x;
