@@ -73,10 +73,10 @@ MULS_PER_FIXED_VARIATE = 34
 # DRAM bytes (read + write) per launch of a dominant kernel, from the ncu
 # capture summarised in profiles/ (None once the kernel changes).  The 256^2
 # kernel was captured on 4 of its 128 replications per design point (256 of
-# 8,192 CTAs: 38,400 B read, 0 written during the launch -- per-CTA design
+# 8,192 CTAs: 37,888 B read, 0 written during the launch -- per-CTA design
 # points, constants and code; the counts stay in L2) and is scaled by the
 # replications of a full launch (x32).
-PROFILED_TRAFFIC = {"forest_fire_kernel<8>": 38400 * 32}
+PROFILED_TRAFFIC = {"forest_fire_kernel<8>": 37888 * 32}
 
 
 # Issue slots: 4 schedulers per SM, one warp instruction each per clock.
