@@ -20,8 +20,9 @@ them against the replication count).
 value   = replications / s over the K timed steps, inputs resident in HBM,
           device time from CUDA events on the launching stream, L2 flushed
           (256 MiB write) between steps outside the timed intervals.
-e2e     = the same through the public model-handle API (mrip_run with host
-          design points + mrip_stats reading the intervals back), wall time.
+e2e     = the same through the public model-handle API (mrip_run with the
+          design points in pinned host memory + mrip_stats reading the
+          intervals back), wall time.
 roofline= the dominant kernel's algorithmic work per launch / its mean event
           time.  Lattices: integer instructions per cell-update against the
           issue rate (SMs x 4 warp instructions per clock x maximum SM clock),
@@ -966,6 +967,9 @@ def e2e_model(wl, model, stream, torch, steps, barrier, world, total_units, shar
     from paper_1501_01405_gb300.distributed import gather_merge_stats
     model.set_stream(stream)
     dps, n_reps = wl.e2e_inputs()
+    # the step's inputs live in pinned host memory (a numpy view of it: the
+    # C ABI takes a plain host pointer)
+    dps = torch.tensor(np.ascontiguousarray(dps, dtype=np.float64)).pin_memory().numpy()
 
     def one():
         if sharded:
