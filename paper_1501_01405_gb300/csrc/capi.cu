@@ -422,6 +422,7 @@ extern "C" mrip_status mrip_set_stream(mrip_model* m, void* cuda_stream) {
 extern "C" mrip_status mrip_run_range(mrip_model* m, const double* design_points, int32_t n_dp, int64_t rep_lo,
                                       int64_t rep_hi, uint64_t seed) {
     if (!m || !design_points) return fail(MRIP_EINVAL, "mrip_run: null argument");
+    NvtxRange range("mrip_run");
     const int64_t n_reps = rep_hi - rep_lo;
     mrip_status s = check_shape(m, n_dp, n_reps, rep_lo);
     if (s != MRIP_OK) return s;
@@ -642,6 +643,7 @@ extern "C" mrip_status mrip_run_cv(mrip_model* m, const double* design_points, i
                                    mrip_cv_stat* cv_out, mrip_cv_report* report) {
     if (!m || !design_points || !params || !plain_out || !cv_out)
         return fail(MRIP_EINVAL, "mrip_run_cv: null argument");
+    NvtxRange range("mrip_run_cv");
     return run_cv_impl(m, design_points, n_dp, n_reps, seed, params, plain_out, cv_out, report);
 }
 

@@ -1031,6 +1031,7 @@ void epoch_affine(uint64_t seed, int epoch, unsigned long long n, unsigned long 
 // float -- and uploads it to library scratch.  Synchronous: reads back
 // whether an MMA completion wait ran out, and the run's counts.
 mrip_status mlp_train(const TrainSpec& sp, TrainInfo* info, cudaStream_t st) {
+    NvtxRange range("mlp_train");
     TrainInfo none{0, 0, 0};
     if (info) *info = none;
     if (sp.n == 0 || sp.epochs == 0) return MRIP_OK;

@@ -223,3 +223,44 @@ def test_two_gloo_ranks_shard_one_experiment(env):
     for rank, merged, hw in got:
         np.testing.assert_allclose(merged, ref, rtol=1e-13, atol=0)
         np.testing.assert_allclose(hw, ref_hw, rtol=1e-13)
+
+
+def test_checkpoint_resume_matches_one_run(env, tmp_path):
+    """An experiment interrupted after two ranges, saved, loaded and resumed
+    in ranges of another size gives the one-run (n, mean, M2) within 1e-13
+    (the merge order is the replication order either way)."""
+    eng, torch = env
+    from paper_1501_01405_gb300.checkpoint import Checkpoint, run_resumable
+    path = str(tmp_path / "exp.json")
+    for kind, params, dps in ((eng.MRIP_MM1, {"n_clients": 400}, [[0.9, 1.0], [0.6, 1.0]]),
+                              (eng.MRIP_WALK_L1_EXIT, {"max_steps": 1 << 30}, [12.0, 5.0])):
+        n, seed = 301, 42
+        m = eng.Model(kind, **params)
+        m.run(dps, n, seed)
+        ref = m.moments()
+        m.close()
+        ck = Checkpoint(kind, params, dps, n, seed)
+        part = run_resumable(ck, 64, path=path, max_chunks=2)
+        assert np.all(part[:, 0] == 128) and not ck.complete()
+        again = Checkpoint.load(path)
+        assert again.missing() == [(128, n)]
+        full = run_resumable(again, 50, path=path)
+        assert again.complete() and Checkpoint.load(path).complete()
+        assert np.array_equal(full[:, 0], ref[:, 0])
+        np.testing.assert_allclose(full[:, 1:], ref[:, 1:], rtol=1e-13, atol=0)
+
+
+def test_allocation_failure_is_reported_and_the_handle_recovers(env):
+    """A run too large for any device (2^20 design points x 2^20 replications:
+    24 TB of outputs) returns MRIP_ENOMEM from a failed allocation -- a
+    normal error return, not a fault -- and the same handle then runs a
+    small experiment."""
+    eng, torch = env
+    m = eng.Model(eng.MRIP_MM1, n_clients=10)
+    big = np.tile([[0.5, 1.0]], (1 << 20, 1))
+    with pytest.raises(eng.MripError) as e:
+        m.run(big, 1 << 20, 42)
+    assert e.value.code == 2
+    m.run([[0.5, 1.0]], 8, 42)
+    assert m.stats()[0]["n"] == 8
+    m.close()
