@@ -169,7 +169,7 @@ mrip_status mrip_run_device(mrip_model *model, const double *d_design_points, in
 mrip_status mrip_stats(mrip_model *model, double conf, mrip_stat *out);
 
 /* Synchronous.  The last run's per-design-point (n, mean, M2) triples
- * (Welford/Chan, FP64) into the caller's host array nmm2_out[n_dp][3]: the
+ * (FP64, as mrip_stats_reduce) into the caller's host array nmm2_out[n_dp][3]: the
  * exact input of mrip_stats_merge when shards of one experiment are
  * combined.  Errors as mrip_stats. */
 mrip_status mrip_moments(mrip_model *model, double *nmm2_out);
@@ -443,12 +443,14 @@ mrip_status mrip_pi_simulate(int64_t rep0, int64_t n_reps, int64_t n_draws, uint
 mrip_status mrip_check_device_flags(void);
 
 /* Per-design-point (n, mean, M2) of d_x (device double [n_dp][n_reps]) by
- * Welford within a thread and a Chan merge across threads in a fixed tree;
- * more than 4,096 replications are cut into slices (one CTA each) merged in
- * slice order (deterministic).  d_out: device double [n_dp][3].  The slice
+ * the two-pass definition (mean = sum / n, then M2 = sum of squared
+ * deviations from it), each sum in a fixed order over 256 threads; more than
+ * 4,096 replications are cut into slices (one CTA each) whose triples are
+ * merged in slice order by Chan's pairwise formula (deterministic).  d_out: device double [n_dp][3].  The slice
  * partials live in library scratch memory, which a later call may grow:
  * capture this call in a CUDA graph only if that graph is replayed before
- * any larger reduction runs (4,096 replications or fewer need no scratch). */
+ * any larger reduction runs (4,096 replications or fewer need no scratch).
+ * With n_reps == 0 d_x may be NULL and every triple is (0, 0, 0). */
 mrip_status mrip_stats_reduce(const double *d_x, int32_t n_dp, int64_t n_reps,
                               double *d_out, void *stream);
 

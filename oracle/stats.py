@@ -5,8 +5,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 The paper builds a confidence interval from replications by the Central Limit
 Theorem and recommends at least 30 replications (Section 1).  With the
 variance estimated from the same replications the interval is
-mean +/- t_{(1+conf)/2, n-1} * sqrt(s^2 / n).  Everything here is the plain
-two-pass definition with exactly rounded sums (math.fsum), FP64.
+mean +/- t_{(1+conf)/2, n-1} * sqrt(s^2 / n).  Everything here is the
+two-pass definition with exactly rounded sums (math.fsum), FP64: s^2 is the
+sum of squared deviations from the exact mean; the deviations are taken
+from the rounded mean m and the sum d of those deviations removes its
+rounding, sum (x - mean)^2 = sum (x - m)^2 - d^2 / n (an identity).
 """
 import math
 
@@ -25,7 +28,8 @@ def dp_stats(x):
     if n < 2:
         return n, mean, float("nan")
     dev = x - mean
-    var = math.fsum((dev * dev).tolist()) / (n - 1)
+    d = math.fsum(dev.tolist())
+    var = (math.fsum((dev * dev).tolist()) - d * d / n) / (n - 1)
     return n, mean, var
 
 

@@ -2,10 +2,10 @@
 // the replication mean and a CLT confidence interval) and the Student-t
 // critical value.
 //
-// Device: one CTA per design point and slice of at most 4,096 replications.
-// Thread t runs Welford's update over the slice's replications t, t + B, ...;
-// the CTA merges the (n, mean, M2) triples pairwise in a fixed tree (Chan,
-// Golub, LeVeque 1979) and a second kernel merges the slices in order, so
+// Device: one CTA per design point and slice of at most 4,096 replications
+// computes the slice's (n, mean, M2) by the two-pass definition in a fixed
+// summation order; a second kernel merges the slices' triples
+// in slice order with Chan, Golub and LeVeque's pairwise formula (1979), so
 // the result does not depend on scheduling.
 //
 // Host: t_{(1+conf)/2, df} from Abramowitz & Stegun 26.7.3/26.7.4 (finite
@@ -23,77 +23,119 @@ namespace mrip {
 namespace {
 
 constexpr int kStatsThreads = 256;
+constexpr int kGroups = kStatsThreads / 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ void chan_merge(double& na, double& ma, double& m2a, double nb, double mb,
-                                           double m2b) {
-    const double n = na + nb;
-    if (nb == 0.0) return;
-    if (na == 0.0) {
-        na = nb;
-        ma = mb;
-        m2a = m2b;
-        return;
-    }
-    const double delta = mb - ma;
-    ma = ma + delta * (nb / n);
-    m2a = m2a + m2b + delta * delta * (na * nb / n);
-    na = n;
+// Sum of a warp's values into lane 0 (fixed shuffle tree).
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(kFull, a, off);
+    return a;
 }
 
-// One CTA per (design point, slice of replications): Welford per thread over
-// the slice, then the CTA's fixed merge tree.  With one slice the triple goes
-// straight to out[dp]; otherwise to part[dp][slice].
+// The 8 warp totals in a fixed pairwise order.
+__device__ __forceinline__ double total8(const double* g) {
+    return ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]));
+}
+
+// One CTA per (design point, slice of replications): (n, mean, M2) of the
+// slice by the corrected two-pass algorithm (Chan, Golub, LeVeque 1983):
+// m = (sum of x) / n, then with d = x - m the exact mean is m + (sum d) / n
+// and M2 = sum d^2 - (sum d)^2 / n; the corrections cancel the first-order
+// effect of the rounding of m (data with a large mean and a small spread).
+// Thread t sums the slice's elements t, t + 256, ... in order; a warp
+// shuffle tree and a fixed sum of the 8 warp totals finish each pass.
+// (Welford's one-pass update with a Chan merge tree across the threads gives
+// the same moments but puts a dependent FP64 division on every element and
+// two on every tree level; on GB300's narrow FP64 pipe that chain was the
+// kernel's whole latency: 12.3k cycles for 32 values and 45k for 4,096,
+// against 4.8k and 11k for the two passes.)  With one slice out[dp] gets
+// (n, m + (sum d) / n, M2); otherwise part[dp][slice] gets the mean as the
+// unrounded pair (n, m, M2, (sum d) / n) for the slice merge.
 template <typename T>
 __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const T* __restrict__ x, long long n_reps,
                                                               int slices, double* __restrict__ out) {
-    __shared__ double sn[kStatsThreads], sm[kStatsThreads], s2[kStatsThreads];
+    __shared__ double gsum[kGroups], gsq[kGroups], gdev[kGroups];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long dp = blockIdx.x / slices;
     const long long sl = blockIdx.x - dp * slices;
     const long long per = (n_reps + slices - 1) / slices;
     const long long lo = sl * per;
     const long long hi = lo + per < n_reps ? lo + per : n_reps;
+    const long long n = hi > lo ? hi - lo : 0;
+    const double inv_n = n > 0 ? 1.0 / static_cast<double>(n) : 0.0;
     const T* row = x + dp * n_reps;
-    double n = 0.0, mean = 0.0, m2 = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += kStatsThreads) {
-        const double v = static_cast<double>(row[i]);
-        n += 1.0;
-        const double d = v - mean;
-        mean += d / n;
-        m2 += d * (v - mean);
-    }
-    sn[threadIdx.x] = n;
-    sm[threadIdx.x] = mean;
-    s2[threadIdx.x] = m2;
+    double a = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kStatsThreads) a += static_cast<double>(row[i]);
+    a = warp_sum(a);
+    if (lane == 0) gsum[warp] = a;
     __syncthreads();
-    for (int stride = kStatsThreads / 2; stride > 0; stride >>= 1) {
-        if (threadIdx.x < stride) {
-            double a = sn[threadIdx.x], b = sm[threadIdx.x], c = s2[threadIdx.x];
-            chan_merge(a, b, c, sn[threadIdx.x + stride], sm[threadIdx.x + stride],
-                       s2[threadIdx.x + stride]);
-            sn[threadIdx.x] = a;
-            sm[threadIdx.x] = b;
-            s2[threadIdx.x] = c;
-        }
-        __syncthreads();
+    const double mean = n > 0 ? total8(gsum) / static_cast<double>(n) : 0.0;
+    double q = 0.0, c = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kStatsThreads) {
+        const double d = static_cast<double>(row[i]) - mean;
+        q += d * d;
+        c += d;
     }
+    q = warp_sum(q);
+    c = warp_sum(c);
+    if (lane == 0) {
+        gsq[warp] = q;
+        gdev[warp] = c;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double* o = out + 3 * blockIdx.x;
-        o[0] = sn[0];
-        o[1] = sm[0];
-        o[2] = s2[0];
+        const double sd = total8(gdev);
+        double m2 = total8(gsq) - sd * sd * inv_n;
+        if (m2 < 0.0) m2 = 0.0;
+        if (slices == 1) {
+            double* o = out + 3 * blockIdx.x;
+            o[0] = static_cast<double>(n);
+            o[1] = mean + sd * inv_n;
+            o[2] = m2;
+        } else {
+            double* o = out + 4 * blockIdx.x;
+            o[0] = static_cast<double>(n);
+            o[1] = mean;
+            o[2] = m2;
+            o[3] = sd * inv_n;
+        }
     }
 }
 
-// Slices of one design point merged in slice order.
+// Slices of one design point merged in slice order by Chan's formula, the
+// running mean kept as an unevaluated pair hi + lo (Knuth's two-sum) so that
+// the difference of two slice means keeps the bits their rounding to one
+// double would lose.
 __global__ void stats_merge_kernel(const double* __restrict__ part, int n_dp, int slices,
                                    double* __restrict__ out) {
     const int dp = blockIdx.x * blockDim.x + threadIdx.x;
     if (dp >= n_dp) return;
-    const double* p = part + static_cast<long long>(dp) * slices * 3;
-    double n = p[0], mean = p[1], m2 = p[2];
-    for (int s = 1; s < slices; ++s) chan_merge(n, mean, m2, p[3 * s], p[3 * s + 1], p[3 * s + 2]);
+    const double* p = part + static_cast<long long>(dp) * slices * 4;
+    double n = p[0], mh = p[1], m2 = p[2], ml = p[3];
+    for (int s = 1; s < slices; ++s) {
+        const double nb = p[4 * s], bh = p[4 * s + 1], m2b = p[4 * s + 2], bl = p[4 * s + 3];
+        if (nb == 0.0) continue;
+        if (n == 0.0) {
+            n = nb;
+            mh = bh;
+            m2 = m2b;
+            ml = bl;
+            continue;
+        }
+        const double nn = n + nb;
+        const double delta = (bh - mh) + (bl - ml);
+        const double t = ml + delta * (nb / nn);
+        const double sh = mh + t;  // two-sum of mh and t
+        const double v = sh - mh;
+        const double sl = (mh - (sh - v)) + (t - v);
+        m2 = m2 + m2b + delta * delta * (n * nb / nn);
+        mh = sh;
+        ml = sl;
+        n = nn;
+    }
     out[3 * dp] = n;
-    out[3 * dp + 1] = mean;
+    out[3 * dp + 1] = mh + ml;
     out[3 * dp + 2] = m2;
 }
 
@@ -217,8 +259,8 @@ double t_critical(double conf, long long df) {
 }
 
 // Replications per slice: few design points with many replications would
-// otherwise run on a few SMs (the FP64 Welford update is ~14 FP64 operations
-// per value on GB300's narrow FP64 pipe).
+// otherwise run on a few SMs (GB300's FP64 pipe is narrow: each value costs
+// two loads and three FP64 operations).
 constexpr long long kStatsSlice = 4096;
 
 int stats_slices(int32_t n_dp, int64_t n_reps) {
@@ -231,7 +273,7 @@ int stats_slices(int32_t n_dp, int64_t n_reps) {
 
 size_t stats_scratch_bytes(int32_t n_dp, int64_t n_reps) {
     const int s = stats_slices(n_dp, n_reps);
-    return s > 1 ? static_cast<size_t>(n_dp) * s * 3 * sizeof(double) : 0;
+    return s > 1 ? static_cast<size_t>(n_dp) * s * 4 * sizeof(double) : 0;
 }
 
 template <typename T>
@@ -282,7 +324,7 @@ using namespace mrip;
 extern "C" mrip_status mrip_stats_reduce(const double* d_x, int32_t n_dp, int64_t n_reps,
                                          double* d_out, void* stream) {
     if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_stats_reduce: negative size");
-    if (n_dp > 0 && (!d_x || !d_out)) return fail(MRIP_EINVAL, "mrip_stats_reduce: null pointer");
+    if (n_dp > 0 && (!d_out || (n_reps > 0 && !d_x))) return fail(MRIP_EINVAL, "mrip_stats_reduce: null pointer");
     const size_t need = stats_scratch_bytes(n_dp, n_reps);
     double* part = need ? static_cast<double*>(scratch(need, 3)) : nullptr;
     if (need && !part) return fail(MRIP_ENOMEM, "mrip_stats_reduce: scratch allocation failed");
@@ -292,7 +334,7 @@ extern "C" mrip_status mrip_stats_reduce(const double* d_x, int32_t n_dp, int64_
 extern "C" mrip_status mrip_stats_reduce_i64(const int64_t* d_x, int32_t n_dp, int64_t n_reps,
                                              double* d_out, void* stream) {
     if (n_dp < 0 || n_reps < 0) return fail(MRIP_EINVAL, "mrip_stats_reduce_i64: negative size");
-    if (n_dp > 0 && (!d_x || !d_out)) return fail(MRIP_EINVAL, "mrip_stats_reduce_i64: null pointer");
+    if (n_dp > 0 && (!d_out || (n_reps > 0 && !d_x))) return fail(MRIP_EINVAL, "mrip_stats_reduce_i64: null pointer");
     const size_t need = stats_scratch_bytes(n_dp, n_reps);
     double* part = need ? static_cast<double*>(scratch(need, 3)) : nullptr;
     if (need && !part) return fail(MRIP_ENOMEM, "mrip_stats_reduce_i64: scratch allocation failed");

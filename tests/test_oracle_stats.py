@@ -74,6 +74,18 @@ def test_two_pass_moments_exact():
                                                                         rel=1e-15)
     k, mean, var = ostats.dp_stats([3.5])
     assert k == 1 and mean == 3.5 and math.isnan(var)
+    # a large mean and a small spread: exact rational arithmetic decides (the
+    # deviations from the rounded mean alone would miss by up to ~1e-10 here)
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    for loc in (1e9, -3e12):
+        x = loc + 1e-2 * rng.standard_normal(777)
+        fx = [Fraction(v) for v in x.tolist()]
+        em = sum(fx) / len(fx)
+        ev = sum((v - em) ** 2 for v in fx) / (len(fx) - 1)
+        k, mean, var = ostats.dp_stats(x)
+        assert mean == float(em)
+        assert var == pytest.approx(float(ev), rel=1e-13)
     c = ostats.ci([1.0, 1.0, 1.0])
     assert c["half_width"] == 0.0 and c["mean"] == 1.0
 

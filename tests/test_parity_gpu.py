@@ -431,6 +431,25 @@ def test_stats_reduce(eng, torch_mod, n_reps):
             assert got[d, 2] == 0.0
 
 
+@pytest.mark.parametrize("n_reps", [1000, 4097, 1 << 17])
+def test_stats_reduce_large_mean_small_spread(eng, torch_mod, n_reps):
+    """Mean 1e9, spread 1e-2: deviations taken from the rounded mean alone
+    (an ulp of 1e9 is 1.2e-7) miss the variance by up to ~1e-10 relative; the
+    corrected two-pass term (the sum of the deviations) removes that, on both
+    sides."""
+    t = torch_mod
+    n_dp = 3
+    x = mrip_inputs.random_matrix((n_dp, n_reps), 5, scale=1e-2, loc=1e9)
+    out = t.empty(n_dp * 3, dtype=t.float64, device="cuda")
+    eng.mrip_stats_reduce(dev(t, x), out)
+    got = out.cpu().numpy().reshape(n_dp, 3)
+    for d in range(n_dp):
+        n, mean, var = ostats.dp_stats(x[d])
+        assert got[d, 0] == n
+        assert got[d, 1] == pytest.approx(mean, rel=1e-14)
+        assert got[d, 2] / (n - 1) == pytest.approx(var, rel=1e-12)
+
+
 def test_stats_reduce_i64(eng, torch_mod):
     t = torch_mod
     rng = np.random.default_rng(4)
@@ -708,3 +727,9 @@ def test_every_stage_accepts_an_empty_batch(eng, torch_mod):
     assert sentinel.cpu().tolist() == [7.0] * 4
     assert counts.cpu().tolist() == [7] * 4 and tau.cpu().tolist() == [7] * 4
     assert fa.cpu().tolist() == [7] * 4
+    # design points without replications: (0, 0, 0) each, the empty input may be NULL
+    z = t.full((9,), 7.0, dtype=t.float64, device="cuda")
+    eng.mrip_stats_reduce(t.empty((3, 0), dtype=t.float64, device="cuda"), z)
+    zi = t.full((6,), 7.0, dtype=t.float64, device="cuda")
+    eng.mrip_stats_reduce_i64(t.empty((2, 0), dtype=t.int64, device="cuda"), zi)
+    assert z.cpu().tolist() == [0.0] * 9 and zi.cpu().tolist() == [0.0] * 6
