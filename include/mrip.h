@@ -442,6 +442,24 @@ mrip_status mrip_pi_simulate(int64_t rep0, int64_t n_reps, int64_t n_draws, uint
  * its step cap (and clears the flag), else MRIP_OK. */
 mrip_status mrip_check_device_flags(void);
 
+/* Synchronous (waits for the whole device).  Bounds checks of a debug build
+ * (the library compiled with -DMRIP_DEBUG; compute-sanitizer's stand-in):
+ * kernels check their data-dependent indices -- event positions, the walk's
+ * work-item decoding, minibatch sample indices, map cells, output ranges --
+ * and the use of dynamically sized shared memory against the launch's
+ * actual size; a failed check records (site, index) and skips the access.
+ * *enabled: 1 in a debug build, 0 otherwise (then *first is 0).  *first:
+ * (site << 40) | (index mod 2^40) of the first failed check since the last
+ * call (sites: forest fire 1xx, queues 2xx, walk 3xx, network 4xx, control
+ * variate 5xx, area walk 6xx, statistics 7xx), 0 if none; the records are
+ * cleared. */
+mrip_status mrip_debug_checks(int32_t *enabled, uint64_t *first);
+
+/* Debug build only: records one deliberately failed check (site 999, index
+ * 12345) that guards no access, so a test can see the record travel to
+ * mrip_debug_checks.  A release build returns MRIP_EINVAL. */
+mrip_status mrip_debug_selftest(void);
+
 /* Per-design-point (n, mean, M2) of d_x (device double [n_dp][n_reps]) by
  * the two-pass definition (mean = sum / n, then M2 = sum of squared
  * deviations from it), each sum in a fixed order over 256 threads; more than

@@ -17,11 +17,11 @@ from ._abi import (MRIP_MAP_AUTO, MRIP_MAP_CTA, MRIP_MAP_PERSISTENT, MRIP_MAP_TH
                    MripLibraryMissing, mrip_cv_params, mrip_cv_report, mrip_cv_stat,
                    mrip_forest_fire_params,
                    mrip_mm1_params, mrip_stat, mrip_tandem3_params, mrip_train_params,
-                   mrip_walk_params, lib, library_path)
+                   mrip_walk_params, lib, library_path, load_library, using_library)
 from ._abi import check as _check
 
 __all__ = [n for n in dir() if n.startswith("mrip_") or n.startswith("MRIP_")] + [
-    "MripError", "MripLibraryMissing", "lib", "library_path", "Model"]
+    "MripError", "MripLibraryMissing", "lib", "library_path", "load_library", "using_library", "Model"]
 
 
 # ---------------------------------------------------------------------------
@@ -156,6 +156,18 @@ def mrip_pi_simulate(n_reps, n_draws, seed, hits, stream=None, rep0=0):
 
 def mrip_check_device_flags():
     _check(lib().mrip_check_device_flags())
+
+
+def mrip_debug_checks(library=None):
+    """(enabled, first) of the bounds checks of a debug build: enabled is
+    False for a release library; first is None or (site, index) of the first
+    failed check since the last call (the records are cleared)."""
+    L = library if library is not None else lib()
+    en = ctypes.c_int32(0)
+    first = ctypes.c_uint64(0)
+    _check(L.mrip_debug_checks(ctypes.byref(en), ctypes.byref(first)))
+    rec = first.value
+    return bool(en.value), (None if rec == 0 else (rec >> 40, rec & ((1 << 40) - 1)))
 
 
 def mrip_stats_reduce(x, out, stream=None):

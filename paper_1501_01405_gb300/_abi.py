@@ -1,4 +1,5 @@
 """ctypes declarations of include/mrip.h (argument marshalling only)."""
+import contextlib
 import ctypes
 import os
 
@@ -112,6 +113,8 @@ SIGNATURES = {
     "mrip_area_walk_simulate": (_INT, [_I64, _I64, _I32, _U64, _INT, _P, _P, _P]),
     "mrip_pi_simulate": (_INT, [_I64, _I64, _I64, _U64, _P, _P]),
     "mrip_check_device_flags": (_INT, []),
+    "mrip_debug_checks": (_INT, [_P, _P]),
+    "mrip_debug_selftest": (_INT, []),
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_reduce_i64": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_finalize": (_INT, [_P, _I32, _D, _P]),
@@ -134,6 +137,17 @@ def library_path():
     return LIB_PATH
 
 
+def load_library(path):
+    """Load an engine library (e.g. the debug variant) with the ABI's
+    signatures, without making it the binding's library."""
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
 def lib():
     """The loaded engine library; raises MripLibraryMissing if it was not built."""
     global _lib
@@ -143,13 +157,20 @@ def lib():
         raise MripLibraryMissing(
             "libmrip.so not found at %s: build it with "
             "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
-    L = ctypes.CDLL(LIB_PATH)
-    for name, (res, args) in SIGNATURES.items():
-        fn = getattr(L, name)
-        fn.restype = res
-        fn.argtypes = args
+    _lib = load_library(LIB_PATH)
+    return _lib
+
+
+@contextlib.contextmanager
+def using_library(L):
+    """Route the binding's calls to the library L for the duration."""
+    global _lib
+    saved = lib()
     _lib = L
-    return L
+    try:
+        yield L
+    finally:
+        _lib = saved
 
 
 def check(code):

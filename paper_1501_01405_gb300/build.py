@@ -5,6 +5,11 @@ Every translation unit under csrc/ is compiled by nvcc in parallel with
 paper_1501_01405_gb300/_build/libmrip.so with the CUDA runtime linked
 statically.  A unit is recompiled only when it or a header is newer than its
 object file.
+
+build(variant="debug") compiles the same sources with -DMRIP_DEBUG (the
+kernels' bounds checks, read by mrip_debug_checks) into
+_build_debug/libmrip_debug.so, linked -Bsymbolic so that it can be loaded
+beside the release library.
 """
 import glob
 import os
@@ -17,6 +22,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmrip.so")
+VARIANTS = {
+    "release": (OUT, LIB, [], []),
+    "debug": (os.path.join(HERE, "_build_debug"), os.path.join(HERE, "_build_debug", "libmrip_debug.so"),
+              ["-DMRIP_DEBUG"], ["-Xlinker", "-Bsymbolic"]),
+}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE]
@@ -35,8 +45,8 @@ def _headers():
     return sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src, extra, out=OUT):
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
@@ -49,26 +59,28 @@ def _compile(src, extra):
     return obj
 
 
-def build(force=False, extra_flags=None, jobs=None):
-    """Compile csrc/*.cu and link _build/libmrip.so; returns the library path."""
-    os.makedirs(OUT, exist_ok=True)
-    extra = list(extra_flags or [])
+def build(force=False, extra_flags=None, jobs=None, variant="release"):
+    """Compile csrc/*.cu and link the variant's library (release:
+    _build/libmrip.so); returns the library path."""
+    out, lib, vflags, lflags = VARIANTS[variant]
+    os.makedirs(out, exist_ok=True)
+    extra = vflags + list(extra_flags or [])
     if force:
-        for o in glob.glob(os.path.join(OUT, "*.o")):
+        for o in glob.glob(os.path.join(out, "*.o")):
             os.remove(o)
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=jobs or min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not force:
-        return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    if os.path.exists(lib) and os.path.getmtime(lib) >= newest and not force:
+        return lib
+    tmp = lib + ".tmp.%d" % os.getpid()
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static"] + lflags + ["-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def ptxas_report():

@@ -47,7 +47,8 @@ __device__ void walk_serial(uint32_t rep, int n_steps, const RoundKeys& rk, uint
         const int n = min(64, n_steps - m0);
         for (int s = 0; s < n; ++s) {
             move((words[s >> 4] >> (2 * (s & 15))) & 3u, x, y);
-            hist[area_of(x, y) * stride] += 1u;
+            const int a = area_of(x, y);
+            if (MRIP_CHECK(a >= 0 && a < kAreas, 601, a)) hist[a * stride] += 1u;
         }
     }
     *final_area = area_of(x, y);
@@ -122,7 +123,8 @@ __global__ void __launch_bounds__(kThreads) area_walk_coop_kernel(long long rep0
         int x = wrap(px + sx - dx, kW), y = wrap(py + sy - dy, kH);
         for (int s = 0; s < cnt; ++s) {
             move((w >> (2 * s)) & 3u, x, y);
-            atomicAdd(&hist[warp][area_of(x, y)], 1u);
+            const int a = area_of(x, y);
+            if (MRIP_CHECK(a >= 0 && a < kAreas, 602, a)) atomicAdd(&hist[warp][a], 1u);
         }
         px = wrap(px + __shfl_sync(kFull, sx, 31), kW);
         py = wrap(py + __shfl_sync(kFull, sy, 31), kH);
@@ -162,3 +164,5 @@ extern "C" mrip_status mrip_area_walk_simulate(int64_t rep0, int64_t n_reps, int
     }
     return launch_status("mrip_area_walk_simulate");
 }
+
+MRIP_DEBUG_UNIT(area_walk)

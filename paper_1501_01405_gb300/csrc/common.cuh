@@ -24,6 +24,56 @@ struct NvtxRange {
 };
 
 // ---------------------------------------------------------------------------
+// Bounds checks of a debug build (-DMRIP_DEBUG).
+//
+// MRIP_CHECK(cond, site, index) guards one access: in a release build it is
+// the constant true and the compiler drops it; in a debug build a false
+// cond records (site, index) in this translation unit's record -- the first
+// failure since the record was last read wins -- and evaluates to false, so
+// the caller skips (or clamps) the access.  Nothing traps, asserts or waits.
+// Sites are numbered per file (forest fire 1xx, queues 2xx, walk 3xx,
+// network 4xx, control variate 5xx, area walk 6xx, statistics 7xx); the
+// host reads and clears the records with mrip_debug_checks.
+// ---------------------------------------------------------------------------
+#ifdef MRIP_DEBUG
+static __device__ unsigned long long g_check_first;
+
+__device__ __forceinline__ bool check_record(bool ok, unsigned site, long long index) {
+    if (!ok) {
+        const unsigned long long rec =
+            (static_cast<unsigned long long>(site) << 40) | (static_cast<unsigned long long>(index) & ((1ull << 40) - 1));
+        atomicCAS(&g_check_first, 0ull, rec);
+    }
+    return ok;
+}
+
+#define MRIP_CHECK(cond, site, index) \
+    (::mrip::check_record(static_cast<bool>(cond), (site), static_cast<long long>(index)))
+
+// The host half of a unit's record: read it and put it back to zero.
+#define MRIP_DEBUG_UNIT(name)                                                       \
+    namespace mrip {                                                                \
+    mrip_status debug_take_##name(unsigned long long* rec) {                        \
+        const unsigned long long zero = 0;                                          \
+        cudaError_t e = cudaMemcpyFromSymbol(rec, g_check_first, sizeof(*rec));     \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_first, &zero, sizeof(zero)); \
+        return e == cudaSuccess ? MRIP_OK : cuda_status(e, "debug checks: " #name); \
+    }                                                                               \
+    }
+#else
+#define MRIP_CHECK(cond, site, index) true
+#define MRIP_DEBUG_UNIT(name)
+#endif
+
+// Bytes of dynamic shared memory this launch was given (the PTX special
+// register), for the debug checks of dynamically sized shared arrays.
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The ten round keys are
 // fixed per seed, so the host expands them once and every kernel reads them
 // from its parameter bank (uniform across the grid, no registers).

@@ -46,6 +46,7 @@ __global__ void gather_planes(const double* __restrict__ src, long long src_plan
     if (i >= n_out) return;
     const long long dp = i / n_sel, r = i - dp * n_sel;
     const long long j = dp * n_reps + r0 + r;
+    if (!MRIP_CHECK(r0 + r < n_reps && j < src_plane, 501, i)) return;
     for (int k = 0; k < d; ++k) dst[k * n_out + i] = src[k * src_plane + j];
 }
 
@@ -55,6 +56,7 @@ __global__ void ff_features(const int32_t* __restrict__ counts, int n_steps, int
                             double cells, double* __restrict__ feat) {
     const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (i >= n_items) return;
+    if (!MRIP_CHECK(window >= 0 && window <= n_steps, 502, window)) return;
     const long long dp = i / n_reps;
     feat[i] = log10(fmax(dps[2 * dp], 1e-30));
     feat[n_items + i] = log10(fmax(dps[2 * dp + 1], 1e-30));
@@ -533,3 +535,5 @@ mrip_status run_cv_impl(mrip_model* m, const double* dps, int32_t n_dp, int64_t 
 }
 
 }  // namespace mrip
+
+MRIP_DEBUG_UNIT(cv)

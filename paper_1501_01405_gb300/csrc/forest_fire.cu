@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
     __shared__ long long red[NWARP];
 
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     const long long item = blockIdx.x;
+    if (!MRIP_CHECK(4u * NWORD * sizeof(uint32_t) <= dynamic_smem_bytes(), 101, NWORD)) return;  // CTA-uniform
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const uint32_t t_grow = threshold32(dps[2 * dp]);
@@ -264,8 +264,9 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
         if ((t & 63) == 0 || t == n_steps) {
             const int chunk = (t - 1) >> 6;
             const int n_slot = t - chunk * 64;
-            ff_flush<TPB>(cnt[chunk & 1], n_slot, counts ? counts + item * n_steps + chunk * 64 : nullptr, true,
-                          my_sum);
+            if (MRIP_CHECK(n_slot >= 1 && n_slot <= 64 && chunk * 64 + n_slot <= n_steps, 102, t))
+                ff_flush<TPB>(cnt[chunk & 1], n_slot, counts ? counts + item * n_steps + chunk * 64 : nullptr,
+                              true, my_sum);
         }
     }
 
@@ -392,8 +393,8 @@ __device__ void draw_events(uint32_t* __restrict__ ev, int n_cells, const GapSca
         }
         const int p0 = pos + (incl - span) + 1 + k0;
         const int p1 = p0 + 1 + k1;
-        if (p0 < n_cells) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
-        if (p1 < n_cells) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
+        if (p0 < n_cells && MRIP_CHECK(p0 >= 0, 103, p0)) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
+        if (p1 < n_cells && MRIP_CHECK(p1 > p0, 104, p1)) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
         pos += __shfl_sync(kFull, incl, 31);
     }
 }
@@ -462,8 +463,8 @@ __device__ void draw_step_events(uint32_t* __restrict__ ev_g, uint32_t* __restri
             const int p0 = (g ? pos_g + before : pos_h) + (incl - span) + 1 + k0;
             const int p1 = p0 + 1 + k1;
             uint32_t* ev = g ? ev_g : ev_h;
-            if (p0 < n_cells) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
-            if (p1 < n_cells) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
+            if (p0 < n_cells && MRIP_CHECK(p0 >= 0, 105, p0)) atomicOr(ev + (p0 >> 5), 1u << (p0 & 31));
+            if (p1 < n_cells && MRIP_CHECK(p1 > p0, 106, p1)) atomicOr(ev + (p1 >> 5), 1u << (p1 & 31));
         }
         if (grow_on) {
             pos_g += total_g;
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
 
     const int lane = threadIdx.x & 31;
     const long long item = blockIdx.x;
+    if (!MRIP_CHECK((4u + 2u * NEV) * NWORD * sizeof(uint32_t) <= dynamic_smem_bytes(), 107, NWORD)) return;
     const uint32_t dp = static_cast<uint32_t>(item / n_reps);
     const uint32_t rep = static_cast<uint32_t>(rep0 + item % n_reps);
     const double p_grow = dps[2 * dp], p_light = dps[2 * dp + 1];
@@ -528,8 +530,9 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_skip_kernel(
         // counts of the steps before t are complete: flush a finished chunk
         if (t > 1 && ((t - 1) & 63) == 0) {
             const int chunk = (t - 2) >> 6;
-            ff_flush<TPB>(cnt[chunk & 1], 64, counts ? counts + item * n_steps + chunk * 64 : nullptr, true,
-                          my_sum);
+            if (MRIP_CHECK(chunk * 64 + 64 <= n_steps, 108, t))
+                ff_flush<TPB>(cnt[chunk & 1], 64, counts ? counts + item * n_steps + chunk * 64 : nullptr, true,
+                              my_sum);
         }
         const uint32_t* cur_t = lattice + ((t - 1) & 1) * 2 * NWORD;
         const uint32_t* cur_b = cur_t + NWORD;
@@ -675,3 +678,5 @@ extern "C" mrip_status mrip_forest_fire_simulate(const double* d_dps, int32_t n_
     return forest_fire_launch(d_dps, n_dp, rep0, n_reps, L, n_steps, density, seed, d_init, d_counts,
                               d_scalar, d_final, static_cast<cudaStream_t>(stream));
 }
+
+MRIP_DEBUG_UNIT(forest_fire)

@@ -147,10 +147,20 @@ __device__ void stage_tile(GradSmem& S, int d_in, const float* __restrict__ X, l
     for (int i = t; i < kTile * kMaxIn; i += kGradThreads) {
         const int s = i / kMaxIn, k = i - s * kMaxIn;
         float v = 0.0f;
-        if (s < n_valid && k < d_in) v = bf(X[k * n_total + sample_of(map, pos0 + s)]);
+        if (s < n_valid && k < d_in) {
+            const long long smp = sample_of(map, pos0 + s);
+            if (MRIP_CHECK(smp >= 0 && smp < n_total, 403, smp)) v = bf(X[k * n_total + smp]);
+        }
         S.xt[s][k] = v;
     }
-    if (t < kTile) S.ys[t] = (t < n_valid) ? Y[sample_of(map, pos0 + t)] : 0.0f;
+    if (t < kTile) {
+        float y = 0.0f;
+        if (t < n_valid) {
+            const long long smp = sample_of(map, pos0 + t);
+            if (MRIP_CHECK(smp >= 0 && smp < n_total, 404, smp)) y = Y[smp];
+        }
+        S.ys[t] = y;
+    }
 }
 
 // Forward and backward passes of the staged tile (batch size B_scale for the
@@ -484,6 +494,13 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
     const int p_lo = rank * slice, p_hi = min(P, p_lo + slice);
     constexpr uint32_t kIdesc = tc::idesc_bf16(kTcRows, H);
     constexpr uint32_t kIdescW1 = tc::idesc_bf16(kTcRows, 16);
+    // (debug build: the layout must fit the launch's shared memory; every CTA
+    // of the cluster computes the same sizes, so all leave together, before
+    // any cluster barrier or tensor-memory allocation)
+    if (!MRIP_CHECK(sizeof(TcSmem) + (2ull * P4 + 2ull * slice) * sizeof(float) <= dynamic_smem_bytes(), 402, P)) {
+        if (t == 0 && rank == 0) atomicExch(err, 1);
+        return;
+    }
 
     if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
     if (t == 0) tc::mbar_init(&S.bar);
@@ -643,7 +660,8 @@ __global__ void __cluster_dims__(kTcCluster, 1, 1) __launch_bounds__(kTcThreads,
             for (long long p0 = lo; p0 < hi; p0 += kTcRows) {
                 const int n_valid = static_cast<int>(min(static_cast<long long>(kTcRows), hi - p0));
                 const bool valid = m < n_valid;
-                const long long smp = valid ? sample_of(smap, p0 + m) : 0;
+                long long smp = valid ? sample_of(smap, p0 + m) : 0;
+                if (valid && !MRIP_CHECK(smp >= 0 && smp < ta.n_tr, 401, smp)) smp = 0;
                 const float y = valid ? ta.Y[smp] : 0.0f;
                 uint32_t mask1, mask2;
                 const float yhat = forward_tile(ta.X, ta.n_tr, smp, valid, mask1, mask2);
@@ -1202,3 +1220,5 @@ extern "C" mrip_status mrip_cv_reduce(const double* d_y, const double* d_g, int6
     if (n_dp > 0 && (!d_y || !d_g || !d_gc || !d_out)) return fail(MRIP_EINVAL, "mrip_cv_reduce: null pointer");
     return cv_reduce(d_y, d_g, n, d_gc, m, n_dp, d_out, static_cast<cudaStream_t>(stream));
 }
+
+MRIP_DEBUG_UNIT(mlp)

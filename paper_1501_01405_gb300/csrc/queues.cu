@@ -196,13 +196,18 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
     const long long hi = (lo + seg < n_clients) ? lo + seg : n_clients;
     double* s_buf = stage + static_cast<size_t>(warp_in_cta) * 2 * seg * 32;
     double* a_buf = s_buf + seg * 32;
+    // staged only where the warp's slice fits the launch's shared memory
+    // (always, unless the host sized it wrong: then the debug build records
+    // it and the variates are recomputed instead)
+    const bool staged =
+        kStage && MRIP_CHECK((warp_in_cta + 1ull) * 2 * seg * 32 * sizeof(double) <= dynamic_smem_bytes(), 201, seg);
 
     // pass 1: the segment's composed map
     MaxPlus f{-INFINITY, 0.0};
     for (long long n = lo; n < hi; ++n) {
         double s, a;
         mm1_client(static_cast<uint32_t>(n), rep, dp, inv_lam, inv_mu, rk, tab, s, a);
-        if (kStage) {
+        if (staged) {
             s_buf[(n - lo) * 32 + lane] = s;
             a_buf[(n - lo) * 32 + lane] = a;
         }
@@ -228,7 +233,7 @@ __global__ void mm1_warp_coop_kernel(const double* __restrict__ dps, long long n
     double sum_w = 0.0, sum_i = 0.0, sum_v = 0.0;
     for (long long n = lo; n < hi; ++n) {
         double s, a;
-        if (kStage) {
+        if (staged) {
             s = s_buf[(n - lo) * 32 + lane];
             a = a_buf[(n - lo) * 32 + lane];
         } else {
@@ -795,6 +800,9 @@ __global__ void __launch_bounds__(1024) mm1_cta_kernel(const double* __restrict_
     const long long lo = min(static_cast<long long>(threadIdx.x) * k, n_clients);
     const long long hi = min(lo + k, n_clients);
     const double inv_n = static_cast<double>(n_clients);
+    // (debug build: a stage larger than the launch's shared memory is
+    // recorded and the variates recomputed)
+    staged = staged && MRIP_CHECK(2ull * k * blockDim.x * sizeof(long long) <= dynamic_smem_bytes(), 202, k);
 
     bool fixed_ok = fix_rate_ok(lam) && fix_rate_ok(mu);
     if (fixed_ok) {
@@ -1157,3 +1165,5 @@ extern "C" mrip_status mrip_tandem3_simulate(const double* d_dps, int32_t n_dp, 
     }
     return launch_status("mrip_tandem3_simulate");
 }
+
+MRIP_DEBUG_UNIT(queues)

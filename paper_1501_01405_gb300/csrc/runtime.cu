@@ -200,6 +200,56 @@ extern "C" mrip_status mrip_expo(const uint32_t* d_lo, const uint32_t* d_hi, con
     return launch_status("mrip_expo");
 }
 
+#ifdef MRIP_DEBUG
+namespace mrip {
+namespace {
+// One deliberately failed check (site 999, index 12345): no access is
+// guarded by it, it only exercises the record.
+__global__ void debug_selftest_kernel() { (void)MRIP_CHECK(threadIdx.x != 0, 999, 12345); }
+}  // namespace
+mrip_status debug_take_runtime(unsigned long long* rec);
+mrip_status debug_take_forest_fire(unsigned long long* rec);
+mrip_status debug_take_queues(unsigned long long* rec);
+mrip_status debug_take_walk(unsigned long long* rec);
+mrip_status debug_take_mlp(unsigned long long* rec);
+mrip_status debug_take_cv(unsigned long long* rec);
+mrip_status debug_take_area_walk(unsigned long long* rec);
+mrip_status debug_take_stats(unsigned long long* rec);
+}  // namespace mrip
+#endif
+
+extern "C" mrip_status mrip_debug_checks(int32_t* enabled, uint64_t* first) {
+    if (!enabled || !first) return fail(MRIP_EINVAL, "mrip_debug_checks: null argument");
+    *first = 0;
+#ifdef MRIP_DEBUG
+    *enabled = 1;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e, "mrip_debug_checks");
+    using Take = mrip_status (*)(unsigned long long*);
+    const Take units[] = {debug_take_runtime, debug_take_forest_fire, debug_take_queues,
+                          debug_take_walk,    debug_take_mlp,         debug_take_cv,
+                          debug_take_area_walk, debug_take_stats};
+    for (Take take : units) {  // every unit is read (and cleared); the first record is kept
+        unsigned long long rec = 0;
+        const mrip_status s = take(&rec);
+        if (s != MRIP_OK) return s;
+        if (*first == 0) *first = rec;
+    }
+#else
+    *enabled = 0;
+#endif
+    return MRIP_OK;
+}
+
+extern "C" mrip_status mrip_debug_selftest(void) {
+#ifdef MRIP_DEBUG
+    debug_selftest_kernel<<<1, 32>>>();
+    return launch_status("mrip_debug_selftest");
+#else
+    return fail(MRIP_EINVAL, "mrip_debug_selftest: not a debug build");
+#endif
+}
+
 extern "C" mrip_status mrip_check_device_flags(void) {
     int* flags = device_error_flags();
     if (!flags) return fail(MRIP_ENOMEM, "device error flags: allocation failed");
@@ -212,3 +262,5 @@ extern "C" mrip_status mrip_check_device_flags(void) {
     }
     return MRIP_OK;
 }
+
+MRIP_DEBUG_UNIT(runtime)

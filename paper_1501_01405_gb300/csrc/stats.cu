@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kStatsThreads) stats_kernel(const T* __restric
     const long long n = hi > lo ? hi - lo : 0;
     const double inv_n = n > 0 ? 1.0 / static_cast<double>(n) : 0.0;
     const T* row = x + dp * n_reps;
+    if (!MRIP_CHECK(lo >= 0 && hi <= n_reps, 701, sl)) return;  // CTA-uniform
     double a = 0.0;
     for (long long i = lo + threadIdx.x; i < hi; i += kStatsThreads) a += static_cast<double>(row[i]);
     a = warp_sum(a);
@@ -400,3 +401,5 @@ extern "C" mrip_status mrip_stats_merge(const double* parts, int32_t n_parts, in
     }
     return MRIP_OK;
 }
+
+MRIP_DEBUG_UNIT(stats)

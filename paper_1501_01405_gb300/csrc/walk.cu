@@ -268,11 +268,22 @@ __device__ __forceinline__ void decode(const WalkJob& job, long long g, int& R, 
         k = static_cast<long long>(__umul64hi(static_cast<unsigned long long>(g), job.reps_magic));
         if (g - k * job.n_reps < 0) --k;
     }
-    const long long r = g - k * job.n_reps;
+    long long r = g - k * job.n_reps;
+    // (debug build: the division and the tables must give a replication of
+    // this launch and an output row inside it; a bad one is recorded and
+    // replaced by item 0)
+    if (!MRIP_CHECK(g >= 0 && g < job.total && r >= 0 && r < job.n_reps, 301, g)) {
+        k = 0;
+        r = 0;
+    }
     rep = static_cast<uint32_t>(job.rep0 + r);
     R = job.radius[k];
     dp = static_cast<uint32_t>(job.dp_of[k]);
     out = static_cast<long long>(dp) * job.n_reps + r;
+    if (!MRIP_CHECK(out < job.total && R >= 1, 302, out)) {
+        out = 0;
+        R = 1;
+    }
 }
 
 // Whole replication on one thread (THREAD and WARP_1LANE mappings).
@@ -540,6 +551,7 @@ struct NoAllocTables {
 
 __global__ void __launch_bounds__(256) walk_noalloc_setup(const __grid_constant__ NoAllocTables t,
                                                           unsigned char* base) {
+    if (!MRIP_CHECK(t.n_dp >= 0 && t.n_dp <= kNoAllocMaxDp, 303, t.n_dp)) return;
     int32_t* d_r = reinterpret_cast<int32_t*>(base + kNoAllocHeader);
     int32_t* d_d = d_r + t.n_dp;
     for (int i = threadIdx.x; i < t.n_dp; i += blockDim.x) {
@@ -671,3 +683,5 @@ extern "C" mrip_status mrip_walk_simulate(const double* radii, int32_t n_dp, int
     return walk_launch(d_r, d_d, n_dp, rep0, n_reps, seed, max_steps, mapping, warps_per_cta, ctas_per_sm,
                        chunk, d_tau, reinterpret_cast<unsigned long long*>(base), st);
 }
+
+MRIP_DEBUG_UNIT(walk)

@@ -180,3 +180,23 @@ def test_cv_and_training_arguments_rejected_on_host():
     # a validation set needs its pointers
     assert L.mrip_mlp_train(8, p16, p16, 10, None, None, 5, ctypes.byref(prm), p16, None, None,
                             None, None, None, None, None, None, None) == 1
+
+
+def test_release_library_has_no_debug_checks():
+    eng = _engine()
+    assert eng.mrip_debug_checks() == (False, None)
+    assert eng.lib().mrip_debug_selftest() == 1  # MRIP_EINVAL: not a debug build
+
+
+def test_debug_variant_builds_and_exports_every_symbol():
+    """The bounds-checked variant (-DMRIP_DEBUG) compiles for sm_103a and
+    exports the same entry points; it is only run on a GPU."""
+    eng = _engine()
+    from paper_1501_01405_gb300 import build
+    path = build.build(variant="debug")
+    assert path != eng.library_path() and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if " T " in l)
+    assert not [n for n in _declared() if n not in exported]
+    eng.load_library(path)  # loads beside the release library
