@@ -86,6 +86,7 @@ ISSUE_PER_CLK_SM = 4
 # Philox4x32-10 block (15-20 integer instructions) plus the bit-parallel
 # rule (32 cells per word); the midpoint 17.5 is the algorithmic figure.
 FF_INSTR_PER_CELL = 17.5
+FF_MUL_WIDE_PER_WORD = 137  # widening multiplies per 32-cell lattice word and step
 
 
 def issue_peak_g():
@@ -186,7 +187,11 @@ class ForestFire(Workload):
                         SMS, ISSUE_PER_CLK_SM, SM_MAX_MHZ),
                     per_unit="%.1f integer instructions per cell-update (1/4 Philox4x32-10 "
                              "block + the bit-parallel rule), 32 per warp instruction"
-                             % FF_INSTR_PER_CELL, alt=alt)
+                             % FF_INSTR_PER_CELL, alt=alt,
+                    mul_wide=dict(work=cells * FF_MUL_WIDE_PER_WORD / 32.0 / 32.0,
+                                  per_unit="%d widening multiplies per 32-cell word and step (8 "
+                                           "Philox blocks x 17, two per-step products shared, "
+                                           "+ 1), 32 per warp instruction" % FF_MUL_WIDE_PER_WORD))
 
     def extra_rates(self, reps_per_s, torch):
         w = self.w
@@ -1162,6 +1167,15 @@ def main():
             "traffic": PROFILED_TRAFFIC.get(rw["kernel"]) if args.n_dp == 0 else None,
             "kernel_ms": kmean, "per_unit": rw["per_unit"],
             "peak_source": rw["peak_source"]}
+    if "mul_wide" in rw:  # the binding unit against its rate measured on this GPU, now
+        mw = rw["mul_wide"]
+        m_ach = mw["work"] / (kmean / 1e3) / 1e9
+        m_peak = wl.eng.mrip_probe_mul_wide() / 1e9
+        roof["measured_unit"] = {"unit": "G warp widening-multiplies/s", "achieved": m_ach,
+                                 "peak": m_peak, "frac": m_ach / m_peak,
+                                 "per_unit": mw["per_unit"],
+                                 "peak_source": "measured by mrip_probe_mul_wide after the timed "
+                                                "steps (every SM full of independent chains)"}
     if "alt" in rw:
         alt = rw["alt"]
         a_ach = alt["work"] / (kmean / 1e3) / 1e9

@@ -455,6 +455,15 @@ mrip_status mrip_check_device_flags(void);
  * cleared. */
 mrip_status mrip_debug_checks(int32_t *enabled, uint64_t *first);
 
+/* Synchronous.  Measured throughput of the widening 32 x 32 -> 64-bit
+ * multiply (two per Philox4x32-10 round; the unit that bounds the Philox
+ * stream): a kernel filling every SM with independent chains of one such
+ * multiply and one logic operation, timed with CUDA events on `stream`
+ * (about a millisecond).  *warp_products_per_s: warp-wide multiplies (32
+ * products each) per second on this GPU at its current clocks.  Errors:
+ * MRIP_EINVAL for a null argument, MRIP_ENOMEM, MRIP_ECUDA. */
+mrip_status mrip_probe_mul_wide(double *warp_products_per_s, void *stream);
+
 /* Debug build only: records one deliberately failed check (site 999, index
  * 12345) that guards no access, so a test can see the record travel to
  * mrip_debug_checks.  A release build returns MRIP_EINVAL. */

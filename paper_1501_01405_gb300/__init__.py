@@ -158,6 +158,13 @@ def mrip_check_device_flags():
     _check(lib().mrip_check_device_flags())
 
 
+def mrip_probe_mul_wide(stream=None):
+    """Measured warp-wide widening multiplies per second (32 products each)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().mrip_probe_mul_wide(ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
 def mrip_debug_checks(library=None):
     """(enabled, first) of the bounds checks of a debug build: enabled is
     False for a release library; first is None or (site, index) of the first

@@ -115,6 +115,7 @@ SIGNATURES = {
     "mrip_check_device_flags": (_INT, []),
     "mrip_debug_checks": (_INT, [_P, _P]),
     "mrip_debug_selftest": (_INT, []),
+    "mrip_probe_mul_wide": (_INT, [_P, _P]),
     "mrip_stats_reduce": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_reduce_i64": (_INT, [_P, _I32, _I64, _P, _P]),
     "mrip_stats_finalize": (_INT, [_P, _I32, _D, _P]),
