@@ -230,16 +230,34 @@ __global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
             const int j = k - y * W;
             const uint32_t tw = cur_t[k];
             const uint32_t bw = cur_b[k];
-            const uint32_t up = cur_b[((y + L - 1) & (L - 1)) * W + j];
-            const uint32_t dn = cur_b[((y + 1) & (L - 1)) * W + j];
-            const uint32_t bwest = cur_b[y * W + ((j + W - 1) & (W - 1))];
-            const uint32_t beast = cur_b[y * W + ((j + 1) & (W - 1))];
+            uint32_t up, dn, bwest, beast;
+            if constexpr (W >= 8) {  // the same words, indexed from k (rows are W words; L W a power of two)
+                up = cur_b[(k + NWORD - W) & (NWORD - 1)];
+                dn = cur_b[(k + W) & (NWORD - 1)];
+                bwest = cur_b[(k & ~(W - 1)) | ((j + W - 1) & (W - 1))];
+                beast = cur_b[(k & ~(W - 1)) | ((j + 1) & (W - 1))];
+            } else {
+                up = cur_b[((y + L - 1) & (L - 1)) * W + j];
+                dn = cur_b[((y + 1) & (L - 1)) * W + j];
+                bwest = cur_b[y * W + ((j + W - 1) & (W - 1))];
+                beast = cur_b[y * W + ((j + 1) & (W - 1))];
+            }
             const uint32_t nb = up | dn | (bw << 1) | (bwest >> 31) | (bw >> 1) | (beast << 31);
             uint32_t g = 0, l = 0;
             const unsigned long long base = 0xD2511F53ull * (8u * static_cast<uint32_t>(k));
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const uint4 b = philox_step(base + 0xD2511F53ull * q, c3, sk, rk);
+                unsigned long long pq = base + 0xD2511F53ull * q;
+                if constexpr (W >= 8) {  // the same sum as an explicit carry chain of two 32-bit adds
+                    const unsigned long long cq = 0xD2511F53ull * q;
+                    uint32_t plo, phi;
+                    asm("add.cc.u32 %0, %2, %4;\n\taddc.u32 %1, %3, %5;"
+                        : "=r"(plo), "=r"(phi)
+                        : "r"(static_cast<uint32_t>(base)), "r"(static_cast<uint32_t>(base >> 32)),
+                          "r"(static_cast<uint32_t>(cq)), "r"(static_cast<uint32_t>(cq >> 32)));
+                    pq = (static_cast<unsigned long long>(phi) << 32) | plo;
+                }
+                const uint4 b = philox_step(pq, c3, sk, rk);
                 or_if_below(g, b.x, t_grow, 1u << (4 * q));
                 or_if_below(g, b.y, t_grow, 1u << (4 * q + 1));
                 or_if_below(g, b.z, t_grow, 1u << (4 * q + 2));
