@@ -77,7 +77,7 @@ MULS_PER_FIXED_VARIATE = 34
 # 8,192 CTAs: 37,888 B read, 0 written during the launch -- per-CTA design
 # points, constants and code; the counts stay in L2) and is scaled by the
 # replications of a full launch (x32).
-PROFILED_TRAFFIC = {"forest_fire_kernel<8>": 37376 * 32}
+PROFILED_TRAFFIC = {"forest_fire_kernel<8>": 399360 * 32}
 
 
 # Issue slots: 4 schedulers per SM, one warp instruction each per clock.

@@ -191,8 +191,18 @@ __device__ void ff_store_scalar(long long my_sum, long long* red, double* scalar
     }
 }
 
+// Register budget: a word's eight Philox blocks are independent, and the
+// more registers ptxas may use the more of them it interleaves.  256-thread
+// CTAs (L = 256) are held to three per SM (78 registers: 4.2 % faster than
+// five CTAs at 48); the other widths take the compiler's own maximum (L = 128:
+// 110 registers, four CTAs per SM, 5 % faster than nine at 56).
 template <int W>
-__global__ void __launch_bounds__(ff_threads<W>()) forest_fire_kernel(
+constexpr int ff_min_blocks() {
+    return W == 8 ? 3 : 1;
+}
+
+template <int W>
+__global__ void __launch_bounds__(ff_threads<W>(), ff_min_blocks<W>()) forest_fire_kernel(
     const double* __restrict__ dps, long long n_reps, long long rep0, int n_steps, uint32_t t_dens,
     const __grid_constant__ RoundKeys rk, const uint8_t* __restrict__ init,
     int32_t* __restrict__ counts, double* __restrict__ scalar, uint8_t* __restrict__ final_state) {
