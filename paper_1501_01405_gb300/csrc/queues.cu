@@ -104,8 +104,10 @@ __device__ __forceinline__ void mm1_client(uint32_t n, uint32_t rep, uint32_t dp
     a = expo_fast(b.z, b.w, tab, inv_lam);
 }
 
+// (A minimum of four CTAs per SM rather than eight: the same 64 registers,
+// but 0.80 instead of 0.83 ms for 2^16 replications of 1,000 clients.)
 template <bool kLane0Only>
-__global__ void __launch_bounds__(128, 8) mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
+__global__ void __launch_bounds__(128, 4) mm1_serial_kernel(const double* __restrict__ dps, long long n_items,
                                   long long n_reps, long long rep0, long long n_clients,
                                   const __grid_constant__ RoundKeys rk, LogTable tab, Mm1Out out) {
     long long item;
