@@ -61,3 +61,14 @@ def test_shard_mode_splits_the_replications():
             ranges.append((wl.rep0, wl.rep0 + wl.w["n_reps"]))
         assert ranges[0][0] == 0 and ranges[-1][1] == n_reps
         assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+
+
+def test_multiply_count_per_lattice_word():
+    """The forest-fire multiply roofline counts, per 32-cell lattice word and
+    step, 8 Philox4x32-10 blocks of 20 widening multiplies less the 3 each
+    that a step shares (round 1's product of the replication word, round 2's
+    product of word 0) or a word shares (round 1's product of the block index,
+    one per word for 8 blocks): 8 x 17 + 1."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.FF_MUL_WIDE_PER_WORD == 8 * (20 - 3) + 1
